@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Throughput of the fused MLP -> voxel walk -> DROP reconstruction on B300.
+
+Workload (default): torso-sized scan, 280x280x96 grid of 1 mm voxels, 1.16e8
+synthetic protons over 180 gantry angles in 2-degree steps, 6 DROP iterations,
+block size 320000, rows recomputed on the fly (A never stored), FP32.
+One step = one pct_solve from the initial iterate (x0 = 1 inside the hull):
+hull entry of every proton, then 6 iterations of per-block fused MLP + walk +
+dot + scatter and the block apply.
+
+Prints ONE JSON line (rank 0).  `value` is proton-rows/s per iteration (rows =
+protons whose path crosses the hull), summed over ranks; `recon_s` is the
+seconds of one reconstruction; `e2e` repeats the metric through the C ABI with
+host buffers (history upload and result download inside the timed region).
+`--impl reference` times the FP64 CPU oracle instead (bounded sample).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "proton-rows/s per iteration and recon seconds at 116M protons; RSP err vs FP64"
+UNIT = "proton-rows/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="torso")
+    p.add_argument("--protons", type=int, default=None, help="override the proton count")
+    p.add_argument("--block", type=int, default=None)
+    p.add_argument("--cta", type=int, default=None)
+    p.add_argument("--cpu-sample", type=int, default=320000)
+    p.add_argument("--ref-sample", type=int, default=100000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+    def __init__(self, pci=None):
+        self.pci = pci
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.pci:
+            cmd += ["-i", self.pci]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+                power.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(self.NAMES, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = [s for s, p in zip(sm, power) if p > 200.0] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax),
+                "power_w_max": max(power), "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _pci_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return "%08x:%02x:%02x.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return None
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work model of the fused kernel (FP32 flops, FMA = 2)
+# ----------------------------------------------------------------------------
+FLOP_PER_SAMPLE = 103   # one MLP sample: Sigma2 moments, Highland factor, 2x2 Kalman gain, 2 planes
+FLOP_PER_SEGMENT = 25   # segment set-up of the voxel walk (direction, length, first crossings)
+FLOP_PER_VISIT = 14     # one face crossing + the visit's dot (FMA x2) or scatter product
+
+
+def fused_flops(n_valid, mean_pts, mean_nnz):
+    samples = max(mean_pts - 2.0, 0.0)
+    segs = max(mean_pts - 1.0, 0.0)
+    per_pass = samples * FLOP_PER_SAMPLE + segs * FLOP_PER_SEGMENT + mean_nnz * FLOP_PER_VISIT
+    return 2.0 * per_pass * n_valid
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1802_01070_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(workload):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "drop_fused_traffic.json")
+    try:
+        d = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_hash") != _kernel_hash():
+        return None
+    per_row = d.get("dram_bytes_per_valid_row")
+    return per_row if per_row else None
+
+
+def _measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg (test infrastructure; timed as it stands)
+# ----------------------------------------------------------------------------
+
+def oracle_solve_timed(cfg, hull_np, hist_np, iters, lam, block):
+    import numpy as np
+
+    import oracle as O
+    geo = O.Geometry(cfg.shape, (cfg.voxel,) * 3, cfg.origin, mask=hull_np)
+    t0 = time.perf_counter()
+    rowptr, j, ln, _ = O.rows(geo, hist_np)
+    A = O.csr(rowptr, j, ln, geo.n_vox)
+    x = O.drop(A, hist_np["wepl"].astype(np.float64), iters, lam, block, hull_np.astype(np.float64))
+    dt = time.perf_counter() - t0
+    valid = int(np.count_nonzero(np.diff(rowptr)))
+    return x, dt, valid, O.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import synth
+    cfg = synth.CONFIGS[args.config]
+    n = min(args.ref_sample, cfg.n_protons)
+    rsp, hull = synth.phantom(cfg)
+    hist = synth.to_numpy(synth.histories(cfg, "cpu", n=n, rsp=rsp))
+    hull_np = hull.numpy()
+    block = args.block or cfg.block
+    times, valid, threads = [], 0, 1
+    for k in range(args.warmup + args.steps):
+        _, dt, valid, threads = oracle_solve_timed(cfg, hull_np, hist, cfg.iters, cfg.lam, block)
+        if k >= args.warmup:
+            times.append(dt)
+    t = statistics.mean(times)
+    value = valid * cfg.iters / t
+    sample = ("first %d protons of the %s scan (%d cross the hull), full %d-iteration DROP "
+              "solve with rows built once, block %d" % (n, cfg.name, valid, cfg.iters, block))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": _config(cfg, block, cfg.n_protons),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
+def _config(cfg, block, n):
+    return {"workload": "%s: %dx%dx%d grid of %g mm voxels, %d protons over %d angles, %d DROP "
+                        "iterations, block %d, fused on-the-fly MLP+walk (A never stored)"
+                        % (cfg.name, *cfg.shape, cfg.voxel, n, cfg.n_angles, cfg.iters, block),
+            "grid": list(cfg.shape), "voxel_mm": cfg.voxel, "protons": n, "angles": cfg.n_angles,
+            "iters": cfg.iters, "block": block, "lambda": cfg.lam, "x0": "1.0 inside hull",
+            "l2": "inputs larger than L2: 48 B of history and 64 B of record per proton are "
+                  "streamed each pass (%.1f GB)" % (n * 112 / 1e9)}
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1802_01070_b300 as pct
+    import synth
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    cfg = synth.CONFIGS[args.config]
+    n = args.protons or cfg.n_protons
+    if n != cfg.n_protons:
+        cfg = synth.scaled(cfg, n)
+    block = args.block or cfg.block
+    rsp, hull = synth.phantom(cfg)
+    hull_np = hull.numpy()
+    hist = synth.histories(cfg, dev, chunk=1 << 24, rsp=rsp)
+    s_cpu = min(args.cpu_sample, n)
+    sample_hist = {k: v[:s_cpu].clone() for k, v in hist.items()}
+    torch.cuda.synchronize(dev)
+
+    ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=local)
+    if args.cta:
+        ctx.set_option(pct.PCT_OPT_CTA_THREADS, args.cta)
+    ctx.load_histories(hist)
+
+    # rows crossing the hull, and the mean path size of a sample (work model)
+    valid = 0
+    for a in range(0, n, 1 << 22):
+        c = min(n, a + (1 << 22)) - a
+        valid += int((ctx.hull_states(a, c)[:, 10] > 0.5).sum().item())
+    ns = min(n, 65536)
+    _, npts = ctx.mlp(0, ns, max_pts=1024)
+    _, _, nnz = ctx.rows(0, ns, max_nnz=2048)
+    ok = npts > 0
+    mean_pts = float(npts[ok].float().mean().item()) if ok.any() else 0.0
+    mean_nnz = float(nnz[ok].float().mean().item()) if ok.any() else 0.0
+
+    x0 = torch.from_numpy(hull_np.astype(np.float32)).to(dev)
+    x = torch.empty_like(x0)
+
+    def step():
+        x.copy_(x0)
+        ctx.solve(x, cfg.iters, cfg.lam, block)
+
+    for _ in range(args.warmup):
+        step()
+    ctx.synchronize()
+
+    pci = _pci_id(torch, dev)
+    clk = ClockSampler(pci)
+    ctx.reset_stats()
+    ctx.set_option(pct.PCT_OPT_TIMING, 1)
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk.start()
+    time.sleep(0.3)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    ctx.synchronize()
+    if dist:
+        dist.barrier()
+    step_ms = e0.elapsed_time(e1) / args.steps
+    launches = int(ctx.stat(pct.PCT_STAT_LAUNCHES))
+    fused_ms = ctx.stat(pct.PCT_STAT_FUSED_MS)
+    fused_n = int(ctx.stat(pct.PCT_STAT_FUSED_LAUNCHES))
+    ctx.set_option(pct.PCT_OPT_TIMING, 0)
+    ctx.reset_stats()
+    if dist:
+        t = torch.tensor([step_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms = float(t.item())
+    value = world * valid * cfg.iters / (step_ms * 1e-3)
+
+    # roofline of the dominant kernel (fused DROP block step)
+    peaks = _measured_peaks()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s
+    avg_launch_s = fused_ms * 1e-3 / max(fused_n, 1)
+    blocks_per_iter = math.ceil(n / block)
+    flops_launch = fused_flops(valid, mean_pts, mean_nnz) / blocks_per_iter
+    achieved = flops_launch / avg_launch_s / 1e12
+    hbm_bytes_launch = (n / blocks_per_iter) * (16 * 4)        # proton records streamed per launch
+    per_row_traffic = _profiled_traffic(cfg.name)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "traffic": (per_row_traffic * valid / blocks_per_iter) if per_row_traffic else None,
+                "kernel": "k_drop_fused", "avg_launch_ms": avg_launch_s * 1e3,
+                "launches_timed": fused_n,
+                "peak_source": "148 SMs x 128 FP32 lanes x 2 x %g MHz (MEASURED_PEAKS sm_max_mhz)" % sm_mhz,
+                "flops_model": "2 passes x (%.1f MLP samples x %d + %.1f segments x %d + %.1f visits x %d) "
+                               "per valid row" % (max(mean_pts - 2, 0), FLOP_PER_SAMPLE,
+                                                  max(mean_pts - 1, 0), FLOP_PER_SEGMENT, mean_nnz,
+                                                  FLOP_PER_VISIT),
+                "hbm_gbs_algorithmic": hbm_bytes_launch / avg_launch_s / 1e9,
+                "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                "fused_share_of_step": (fused_ms / args.steps) / step_ms if step_ms else None}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": _config(cfg, block, n), "recon_s": step_ms * 1e-3,
+           "rows_in_hull": valid, "mean_nnz_per_row": mean_nnz, "mean_mlp_points": mean_pts,
+           "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+
+    # end to end through the C ABI with pinned host buffers
+    if not args.no_e2e:
+        host = {k: v.cpu().pin_memory() for k, v in hist.items()}
+        xh = torch.from_numpy(hull_np.astype(np.float32)).pin_memory()
+        del hist
+        torch.cuda.empty_cache()
+        h2d = sum(v.numel() * 4 for v in host.values()) + xh.numel() * 4
+        times = []
+        for k in range(3):
+            xw = xh.clone().pin_memory()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            ctx.load_histories(host)
+            ctx.solve_host(xw.numpy(), cfg.iters, cfg.lam, block)
+            times.append(time.perf_counter() - t0)
+        te = statistics.mean(times[1:])
+        if dist:
+            t = torch.tensor([te], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        out["e2e"] = {"value": world * valid * cfg.iters / te, "unit": UNIT,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": xh.numel() * 4,
+                      "recon_s": te}
+    else:
+        del hist
+
+    # CPU oracle baseline and FP64 parity on a bounded sample (rank 0, N = 1)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = s_cpu
+        sub = sample_hist
+        sub_np = synth.to_numpy(sub)
+        xo, dt, vs, threads = oracle_solve_timed(cfg, hull_np, sub_np, cfg.iters, cfg.lam, block)
+        with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=local) as c2:
+            c2.load_histories(sub)
+            xg = torch.from_numpy(hull_np.astype(np.float32)).to(dev)
+            c2.solve(xg, cfg.iters, cfg.lam, block)
+            c2.synchronize()
+            xg = xg.cpu().numpy().astype(np.float64)
+        hm = hull_np.astype(bool)
+        diff = _structure_diff(ctx_rows_counts(pct, cfg, hull_np, sub, local, block), xo_counts(
+            cfg, hull_np, sub_np, block))
+        rel_all = np.abs(xg - xo) / np.maximum(np.abs(xo), 1e-30)
+        rel = rel_all[hm]
+        clean = hm & ~diff
+        out["cpu_baseline"] = {"value": vs * cfg.iters / dt, "unit": UNIT, "cores": threads,
+                               "kind": "oracle",
+                               "sample": "first %d protons (%d cross the hull): rows built once, "
+                                         "%d DROP iterations, block %d, FP64, %.1f s"
+                                         % (s, vs, cfg.iters, block, dt)}
+        out["rsp_err_vs_fp64"] = {
+            "max_rel_same_structure": float(rel_all[clean].max()),
+            "voxels_structure_differs": int((hm & diff).sum()),
+            "max_rel_all": float(rel.max()), "mean_rel_all": float(rel.mean()),
+            "frac_within_1e-3": float((rel <= 1e-3).mean()), "hull_voxels": int(hm.sum()),
+            "sample": "same %d-proton sample, GPU FP32 fused vs oracle FP64; 'same structure' = hull "
+                      "voxels whose DROP count s_j is identical on both sides in every block (a "
+                      "grazing chord resolved on one side only changes s_j)" % s}
+    if rank == 0:
+        print(json.dumps(out))
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def ctx_rows_counts(pct, cfg, hull_np, sub, local, block):
+    """Per-block visit counts s_j of the GPU rows of a history sample."""
+    import numpy as np
+    import torch
+    n = int(sub["wepl"].numel())
+    nv = cfg.n_vox
+    nb = (n + block - 1) // block
+    counts = np.zeros(nb * nv, dtype=np.int64)
+    with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=local) as c:
+        c.load_histories(sub)
+        for a in range(0, n, 16384):
+            k = min(n, a + 16384) - a
+            idx, _, nnz = c.rows(a, k, max_nnz=1024)
+            nnz = torch.clamp(nnz, max=1024)
+            keep = torch.arange(1024, device=idx.device)[None, :] < nnz[:, None].long()
+            rows = (torch.arange(a, a + k, device=idx.device)[:, None] // block).expand(-1, 1024)
+            key = rows[keep].long() * nv + idx[keep].long()
+            counts += np.bincount(key.cpu().numpy(), minlength=nb * nv)
+    return counts.reshape(nb, nv)
+
+
+def xo_counts(cfg, hull_np, sub_np, block):
+    """Per-block counts s_j of the oracle rows (one per row and voxel)."""
+    import numpy as np
+
+    import oracle as O
+    geo = O.Geometry(cfg.shape, (cfg.voxel,) * 3, cfg.origin, mask=hull_np)
+    rowptr, j, ln, _ = O.rows(geo, sub_np)
+    m = rowptr.size - 1
+    nv = cfg.n_vox
+    nb = (m + block - 1) // block
+    rows = np.repeat(np.arange(m), np.diff(rowptr))
+    key = np.unique(rows.astype(np.int64) * nv + j)
+    blk = (key // nv) // block
+    return np.bincount(blk * nv + key % nv, minlength=nb * nv).reshape(nb, nv)
+
+
+def _structure_diff(cg, co):
+    return (cg != co).any(axis=0)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,199 @@
+/*
+ * pct.h -- C ABI of libpct: proton-CT reconstruction of relative stopping
+ * power (RSP) on one NVIDIA B300 (sm_103a).
+ *
+ * The library implements the data-parallel hot path of Karbasi et al.,
+ * "A Highly Accelerated Parallel Multi-GPU based Reconstruction Algorithm for
+ * Generating Accurate Relative Stopping Powers" (arXiv:1802.01070):
+ *   Sec. I   -- the linear system A x = b: A (m x n) holds the path data of the
+ *               m protons, b their water-equivalent path lengths (WEPL), x the
+ *               RSP of the n voxels; each row follows the proton's most likely
+ *               path (MLP), one proton per thread.
+ *   Sec. IV-B -- the DROP block-iterative solver; a block is the set of protons
+ *               processed in parallel.
+ * Rows of A are recomputed on the fly from the proton histories (MLP, then a
+ * voxel walk along the MLP polyline) and never stored.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns a pct_status; nothing aborts or throws across the ABI.
+ *    On failure pct_last_error(ctx) returns a message, valid until the next
+ *    call on that context.
+ *  - Device pointers ("device") are owned by the caller and must stay valid
+ *    until the work enqueued on the context's stream has finished.  Calls that
+ *    take device pointers only enqueue work: they return before the GPU has
+ *    finished and do not report errors that happen on the GPU; the next
+ *    pct_synchronize() does.
+ *  - A context is not thread-safe: use one context per host thread.
+ *  - Voxel (ix, iy, iz) covers [o + i*d, o + (i+1)*d) on each axis and has
+ *    linear index j = ix + nx*(iy + ny*iz); volumes are float32 arrays of
+ *    nx*ny*nz values in that order.
+ *  - Proton i of the loaded set is row i of A; protons whose straight tracker
+ *    lines miss the hull have an empty row (A x gives 0 there, the solver skips
+ *    them).
+ */
+#ifndef PCT_H_
+#define PCT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pct_ctx pct_ctx;
+
+typedef enum pct_status {
+    PCT_OK = 0,
+    PCT_ERR_ARG = 1,     /* invalid argument: null pointer, size or range */
+    PCT_ERR_CUDA = 2,    /* a CUDA runtime call or kernel launch failed */
+    PCT_ERR_OOM = 3,     /* device allocation failed or would exceed the memory cap */
+    PCT_ERR_STATE = 4,   /* call out of order, e.g. no histories loaded */
+    PCT_ERR_TIMEOUT = 5, /* a bounded device-side wait gave up */
+    PCT_ERR_DEVICE = 6   /* a device-side check failed (see pct_last_error) */
+} pct_status;
+
+/* Reconstruction grid.  Voxel edges in mm; (ox, oy, oz) is the lab position
+ * (mm) of the corner of voxel (0, 0, 0). */
+typedef struct pct_grid {
+    int32_t nx, ny, nz;
+    float dx, dy, dz;
+    float ox, oy, oz;
+} pct_grid;
+
+/* Keys of pct_set_option / pct_get_option. */
+enum pct_option {
+    /* Threads of one CUDA block of the per-proton kernels: 32..512, multiple
+     * of 32.  Default 256.  Performance only. */
+    PCT_OPT_CTA_THREADS = 1,
+    /* MLP sample spacing along the beam depth, in micrometres.  Default: the
+     * smallest voxel edge.  Changes A (both the solver and any reference that
+     * is compared with it must use the same spacing). */
+    PCT_OPT_MLP_STEP_UM = 2,
+    /* Device-memory cap in bytes for the context's own allocations; 0 = none.
+     * An allocation that would pass it fails with PCT_ERR_OOM. */
+    PCT_OPT_MEM_CAP_BYTES = 3,
+    /* 1: record CUDA events around each launch of the fused DROP kernel so that
+     * pct_get_stat(PCT_STAT_FUSED_MS) reports its device time.  Default 0. */
+    PCT_OPT_TIMING = 4
+};
+
+/* Keys of pct_get_stat.  Counters cover the calls since pct_reset_stats. */
+enum pct_stat {
+    PCT_STAT_LAUNCHES = 1,        /* kernels launched by the library */
+    PCT_STAT_FUSED_LAUNCHES = 2,  /* launches of the fused DROP kernel */
+    PCT_STAT_FUSED_MS = 3,        /* their summed device time, ms (needs PCT_OPT_TIMING;
+                                     synchronizes the stream) */
+    PCT_STAT_DEVICE_BYTES = 4,    /* device memory held by the context */
+    PCT_STAT_N_PROTONS = 5,       /* protons loaded */
+    PCT_STAT_N_HULL_VOXELS = 6    /* voxels inside the hull mask */
+};
+
+/* Create a context on CUDA device `device`.
+ *   grid       -- host pointer, copied.
+ *   hull_mask  -- host pointer to nx*ny*nz bytes (nonzero = inside the object
+ *                 hull), copied; NULL means every voxel is inside.  Rows only
+ *                 cover hull voxels (x outside the hull never changes).
+ *   cuda_stream-- a cudaStream_t to enqueue all work on (cudaStreamLegacy,
+ *                 0x1, selects the legacy default stream), or NULL for a
+ *                 non-blocking stream the context creates and owns.
+ * The hull is not part of the paper; the reading used is that a proton's path
+ * starts where its straight entry tracker line first enters a hull voxel and
+ * ends where its straight exit tracker line, followed backwards, first does.
+ * Errors: PCT_ERR_ARG (null out/grid, non-positive sizes, grid over 2^31
+ * voxels), PCT_ERR_CUDA, PCT_ERR_OOM. */
+pct_status pct_create(pct_ctx **out, const pct_grid *grid, const uint8_t *hull_mask, int device,
+                      void *cuda_stream);
+
+/* Release every device allocation of the context (after synchronizing its
+ * stream) and the context itself.  NULL is ignored. */
+void pct_destroy(pct_ctx *ctx);
+
+/* Message of the last failure on ctx (or of the last failed pct_create when
+ * ctx is NULL). */
+const char *pct_last_error(const pct_ctx *ctx);
+
+pct_status pct_set_option(pct_ctx *ctx, int32_t key, int64_t value);
+pct_status pct_get_option(const pct_ctx *ctx, int32_t key, int64_t *value);
+
+/* Load n proton histories (Sec. I: tracker data and WEPL), replacing any
+ * previous set.  Every argument points to n float32 values:
+ *   in_xyz[0..2]   -- entry tracker point, lab frame, mm
+ *   out_xyz[0..2]  -- exit tracker point, lab frame, mm
+ *   ang_in[0..1]   -- entry direction angles in rad: theta in the t-u plane,
+ *                     psi in the v-u plane of the beam frame
+ *   ang_out[0..1]  -- exit direction angles, same convention
+ *   gantry_rad     -- gantry angle phi; beam frame u = (cos phi, sin phi, 0),
+ *                     t = (-sin phi, cos phi, 0), v = z
+ *   wepl_mm        -- measured WEPL (b of A x = b), mm
+ * ptrs_on_device = 1: all pointers are device pointers (copied on the stream,
+ * asynchronously); 0: host pointers (copied, then the call synchronizes, so
+ * the host buffers may be reused on return; pinned buffers copy fastest).
+ * The library keeps its own copy; the caller keeps ownership.  n = 0 is valid.
+ * Errors: PCT_ERR_ARG (n < 0 or a null pointer with n > 0), PCT_ERR_OOM,
+ * PCT_ERR_CUDA. */
+pct_status pct_load_histories(pct_ctx *ctx, int64_t n, const float *const in_xyz[3],
+                              const float *const out_xyz[3], const float *const ang_in[2],
+                              const float *const ang_out[2], const float *gantry_rad,
+                              const float *wepl_mm, int ptrs_on_device);
+
+/* Hull-frame state of protons [first, first+count) (device out, count*12
+ * float32, row-major per proton): u_in, u_out (beam-frame depth of the hull
+ * entry and exit, mm), t0, theta0, v0, psi0 (entry state), t2, theta2, v2, psi2
+ * (exit state), valid (1.0 / 0.0), spare.  Errors: PCT_ERR_ARG, PCT_ERR_STATE. */
+pct_status pct_hull_states(pct_ctx *ctx, int64_t first, int64_t count, float *out_states);
+
+/* MLP polylines of protons [first, first+count) (Sec. I, most likely path):
+ * the hull entry point, the MLP at depths u_in + k*du (k >= 1, below u_out by
+ * more than du/1000) and the hull exit point, in lab mm.
+ *   out_xyz  -- device, count*max_pts*3 float32; proton p's points at
+ *               out_xyz[(p*max_pts + k)*3 + {0,1,2}], at most max_pts written
+ *   out_npts -- device, count int32: the full point count (0 = empty row); a
+ *               count above max_pts means the polyline was cut short
+ * Errors: PCT_ERR_ARG (range, max_pts < 2, null), PCT_ERR_STATE. */
+pct_status pct_mlp(pct_ctx *ctx, int64_t first, int64_t count, int32_t max_pts, float *out_xyz,
+                   int32_t *out_npts);
+
+/* Rows of A for protons [first, first+count), in path order: each entry is one
+ * visit of the MLP polyline to a hull voxel (a maximal run of the path inside
+ * that voxel) with its chord length a_ij in mm.
+ *   out_idx  -- device, count*max_nnz int32 voxel indices
+ *   out_len  -- device, count*max_nnz float32 chord lengths, mm
+ *   out_nnz  -- device, count int32 full row lengths (above max_nnz: cut short)
+ * Errors: PCT_ERR_ARG, PCT_ERR_STATE. */
+pct_status pct_rows(pct_ctx *ctx, int64_t first, int64_t count, int32_t max_nnz, int32_t *out_idx,
+                    float *out_len, int32_t *out_nnz);
+
+/* y = A x (device x: n voxels; device y: m = protons loaded, overwritten). */
+pct_status pct_forward(pct_ctx *ctx, const float *x, float *y);
+
+/* g = A^T y (device y: m values; device g: n voxels, overwritten). */
+pct_status pct_adjoint(pct_ctx *ctx, const float *y, float *g);
+
+/* DROP reconstruction (Sec. IV-B): `iters` passes over the protons in blocks
+ * of `block_size` consecutive rows; for each block, with x frozen,
+ *   x_j <- x_j + lambda / s_j * sum_{i in block} a_ij (b_i - a_i.x) / ||a_i||^2
+ * where s_j counts the rows of the block that cross voxel j (voxels no row
+ * crosses are unchanged; empty rows are skipped).
+ *   x -- device, n float32: the initial iterate on entry, the RSP on return.
+ * Enqueued on the context stream; pct_synchronize reports device errors.
+ * Errors: PCT_ERR_ARG (null x, iters < 0, block_size < 1), PCT_ERR_STATE,
+ * PCT_ERR_OOM, PCT_ERR_CUDA. */
+pct_status pct_solve(pct_ctx *ctx, int32_t iters, float lambda, int64_t block_size, float *x);
+
+/* As pct_solve, with x in host memory: copies x to the device, solves, copies
+ * the result back and synchronizes. */
+pct_status pct_solve_host(pct_ctx *ctx, int32_t iters, float lambda, int64_t block_size,
+                          float *x_host);
+
+/* Wait for the context's stream; report asynchronous CUDA errors
+ * (PCT_ERR_CUDA) and device-side check failures (PCT_ERR_DEVICE). */
+pct_status pct_synchronize(pct_ctx *ctx);
+
+pct_status pct_get_stat(pct_ctx *ctx, int32_t key, double *value);
+pct_status pct_reset_stats(pct_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCT_H_ */

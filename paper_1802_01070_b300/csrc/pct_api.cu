@@ -1,0 +1,610 @@
+// pct_api.cu -- the C ABI of libpct (declared in include/pct.h): context
+// lifetime, device memory, history upload, and the host-side loops that drive
+// the kernels of pct_kernels.cu.  No call aborts or throws across the ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "pct.h"
+#include "pct_internal.h"
+
+using namespace pct;
+
+namespace {
+
+// 1/(beta^2 p^2) of a 200 MeV proton in water, polynomial in depth (cm), MeV^-2:
+// the energy-loss fit used with the most-likely-path formalism.
+const double kCoef200[6] = {7.457e-6, 4.548e-7, -5.777e-8, 1.301e-8, -9.228e-10, 2.687e-11};
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct pct_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    pct_grid grid{};
+    GridC gc{};
+    int64_t n_vox = 0;
+    int64_t n_hull = 0;
+    uint8_t* d_mask = nullptr;
+    float4* d_sig1 = nullptr;
+    int kmax = 0;
+    int64_t du_um = 0;
+    unsigned* d_flags = nullptr;
+    bool loaded = false;                 // pct_load_histories has succeeded once
+    int64_t n = 0, stride = 0, cap = 0;  // protons, column stride, column capacity
+    float* d_hist = nullptr;
+    float* d_rec = nullptr;
+    float2* d_acc = nullptr;
+    float* d_xtmp = nullptr;
+    int cta = 256;
+    int timing = 0;
+    int64_t mem_cap = 0;
+    int64_t mem_used = 0;
+    std::unordered_map<void*, size_t> sizes;
+    int64_t launches = 0;
+    int64_t fused_launches = 0;
+    std::vector<cudaEvent_t> ev;   // pairs (start, stop) of timed fused launches
+    size_t ev_used = 0;
+    std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+pct_status fail(pct_ctx* c, pct_status s, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+pct_status cuda_fail(pct_ctx* c, cudaError_t e, const char* where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(c, e == cudaErrorMemoryAllocation ? PCT_ERR_OOM : PCT_ERR_CUDA, m);
+}
+
+pct_status dalloc(pct_ctx* c, void** p, size_t bytes, const char* what)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (c->mem_cap > 0 && c->mem_used + (int64_t)bytes > c->mem_cap)
+        return fail(c, PCT_ERR_OOM, std::string(what) + ": device memory cap exceeded");
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, PCT_ERR_OOM, std::string(what) + ": cudaMalloc failed (" + cudaGetErrorString(e) + ")");
+    }
+    c->sizes[*p] = bytes;
+    c->mem_used += (int64_t)bytes;
+    return PCT_OK;
+}
+
+void dfree(pct_ctx* c, void* p)
+{
+    if (!p) return;
+    auto it = c->sizes.find(p);
+    if (it != c->sizes.end()) {
+        c->mem_used -= (int64_t)it->second;
+        c->sizes.erase(it);
+    }
+    cudaFree(p);
+}
+
+// Sigma(0, w) for the MLP (w in cm): moments int_0^w (w-u)^n f(u) du of the
+// depth polynomial f, via int_0^w (w-u)^n u^k du = w^(n+k+1) n! k! / (n+k+1)!,
+// times the Highland prefactor E0^2 (1 + 0.038 ln(w/X0))^2 / X0.
+void sigma_from_entry(double w, double S[3])
+{
+    static const double fact[10] = {1, 1, 2, 6, 24, 120, 720, 5040, 40320, 362880};
+    double mom[3] = {0.0, 0.0, 0.0};
+    for (int n = 0; n < 3; ++n)
+        for (int k = 0; k < 6; ++k)
+            mom[n] += kCoef200[k] * std::pow(w, n + k + 1) * fact[n] * fact[k] / fact[n + k + 1];
+    const double lf = 1.0 + 0.038 * std::log(w / (double)kX0);
+    const double pre = (double)kE0 * (double)kE0 * lf * lf / (double)kX0;
+    S[0] = pre * mom[2];
+    S[1] = pre * mom[1];
+    S[2] = pre * mom[0];
+}
+
+double step_mm(const pct_ctx* c)
+{
+    return c->du_um > 0 ? (double)c->du_um * 1e-3
+                        : (double)std::fmin(c->grid.dx, std::fmin(c->grid.dy, c->grid.dz));
+}
+
+pct_status build_sigma_table(pct_ctx* c)
+{
+    const double du = step_mm(c);
+    const double diag = std::sqrt(std::pow((double)c->grid.nx * c->grid.dx, 2) +
+                                  std::pow((double)c->grid.ny * c->grid.dy, 2) +
+                                  std::pow((double)c->grid.nz * c->grid.dz, 2));
+    const int kmax = (int)std::ceil(diag / du) + 3;
+    if (kmax > (1 << 22)) return fail(c, PCT_ERR_ARG, "MLP step too small for this grid");
+    std::vector<float4> tab((size_t)kmax + 1);
+    tab[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 1; k <= kmax; ++k) {
+        double S[3];
+        sigma_from_entry(k * du * 0.1, S);
+        tab[k] = make_float4((float)S[0], (float)S[1], (float)S[2], 0.f);
+    }
+    void* p = nullptr;
+    pct_status s = dalloc(c, &p, tab.size() * sizeof(float4), "MLP table");
+    if (s != PCT_OK) return s;
+    cudaError_t e = cudaMemcpy(p, tab.data(), tab.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dfree(c, p);
+        return cuda_fail(c, e, "MLP table upload");
+    }
+    dfree(c, c->d_sig1);
+    c->d_sig1 = (float4*)p;
+    c->kmax = kmax;
+    return PCT_OK;
+}
+
+Geo geo_of(const pct_ctx* c)
+{
+    Geo G;
+    G.g = c->gc;
+    const double du = step_mm(c);
+    G.mc.du_mm = (float)du;
+    G.mc.du_cm = (float)(0.1 * du);
+    G.mc.dend_mm = (float)(1e-3 * du);
+    for (int k = 0; k < 6; ++k) G.mc.coef[k] = (float)kCoef200[k];
+    G.mc.sig1 = c->d_sig1;
+    G.mc.kmax = c->kmax;
+    G.mask = c->d_mask;
+    G.flags = c->d_flags;
+    return G;
+}
+
+Launch launch_of(pct_ctx* c)
+{
+    return Launch{c->stream, c->cta, &c->launches};
+}
+
+pct_status need_histories(pct_ctx* c)
+{
+    if (!c->loaded) return fail(c, PCT_ERR_STATE, "no proton histories loaded");
+    return PCT_OK;
+}
+
+pct_status prepare(pct_ctx* c)
+{
+    if (c->n == 0) return PCT_OK;
+    cudaError_t e = launch_prepare(launch_of(c), geo_of(c), c->d_hist, c->stride, c->n, c->d_rec);
+    if (e != cudaSuccess) return cuda_fail(c, e, "prepare kernel");
+    return PCT_OK;
+}
+
+pct_status ensure_acc(pct_ctx* c)
+{
+    if (c->d_acc) return PCT_OK;
+    void* p = nullptr;
+    pct_status s = dalloc(c, &p, (size_t)c->n_vox * sizeof(float2), "DROP accumulator");
+    if (s != PCT_OK) return s;
+    c->d_acc = (float2*)p;
+    return PCT_OK;
+}
+
+cudaEvent_t next_event(pct_ctx* c)
+{
+    if (c->ev_used == c->ev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        c->ev.push_back(e);
+    }
+    return c->ev[c->ev_used++];
+}
+
+}  // namespace
+
+extern "C" {
+
+pct_status pct_create(pct_ctx** out, const pct_grid* grid, const uint8_t* hull_mask, int device,
+                      void* cuda_stream)
+{
+    if (!out || !grid) {
+        g_create_error = "pct_create: null argument";
+        return PCT_ERR_ARG;
+    }
+    *out = nullptr;
+    const pct_grid& G = *grid;
+    if (G.nx < 1 || G.ny < 1 || G.nz < 1 || !(G.dx > 0.f) || !(G.dy > 0.f) || !(G.dz > 0.f) ||
+        !std::isfinite(G.dx) || !std::isfinite(G.dy) || !std::isfinite(G.dz) || !std::isfinite(G.ox) ||
+        !std::isfinite(G.oy) || !std::isfinite(G.oz)) {
+        g_create_error = "pct_create: invalid grid";
+        return PCT_ERR_ARG;
+    }
+    const int64_t n_vox = (int64_t)G.nx * G.ny * G.nz;
+    if (n_vox > 0x7fffffffLL) {
+        g_create_error = "pct_create: grid over 2^31 voxels";
+        return PCT_ERR_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        g_create_error = "pct_create: no such CUDA device";
+        return PCT_ERR_ARG;
+    }
+    pct_ctx* c = new (std::nothrow) pct_ctx();
+    if (!c) {
+        g_create_error = "pct_create: out of host memory";
+        return PCT_ERR_OOM;
+    }
+    DeviceGuard dg(device);
+    c->device = device;
+    c->grid = G;
+    c->n_vox = n_vox;
+    c->gc.nx = G.nx;
+    c->gc.ny = G.ny;
+    c->gc.nz = G.nz;
+    c->gc.dx = G.dx;
+    c->gc.dy = G.dy;
+    c->gc.dz = G.dz;
+    c->gc.ox = G.ox;
+    c->gc.oy = G.oy;
+    c->gc.oz = G.oz;
+    c->gc.idx = 1.f / G.dx;
+    c->gc.idy = 1.f / G.dy;
+    c->gc.idz = 1.f / G.dz;
+    pct_status s = PCT_OK;
+    cudaError_t e;
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("pct_create: stream: ") + cudaGetErrorString(e);
+            delete c;
+            return PCT_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    std::vector<uint8_t> mask((size_t)n_vox, 1);
+    if (hull_mask)
+        for (int64_t j = 0; j < n_vox; ++j) mask[(size_t)j] = hull_mask[j] ? 1 : 0;
+    for (int64_t j = 0; j < n_vox; ++j) c->n_hull += mask[(size_t)j];
+    void* p = nullptr;
+    if ((s = dalloc(c, &p, (size_t)n_vox, "hull mask")) == PCT_OK) {
+        c->d_mask = (uint8_t*)p;
+        e = cudaMemcpy(c->d_mask, mask.data(), (size_t)n_vox, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) s = cuda_fail(c, e, "hull mask upload");
+    }
+    if (s == PCT_OK && (s = dalloc(c, &p, sizeof(unsigned), "flags")) == PCT_OK) {
+        c->d_flags = (unsigned*)p;
+        e = cudaMemset(c->d_flags, 0, sizeof(unsigned));
+        if (e != cudaSuccess) s = cuda_fail(c, e, "flags");
+    }
+    if (s == PCT_OK) s = build_sigma_table(c);
+    if (s != PCT_OK) {
+        g_create_error = "pct_create: " + c->err;
+        pct_destroy(c);
+        return s;
+    }
+    *out = c;
+    return PCT_OK;
+}
+
+void pct_destroy(pct_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard dg(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->sizes) cudaFree(kv.first);
+    c->sizes.clear();
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* pct_last_error(const pct_ctx* c)
+{
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
+{
+    if (!c) return PCT_ERR_ARG;
+    DeviceGuard dg(c->device);
+    switch (key) {
+    case PCT_OPT_CTA_THREADS:
+        if (value < 32 || value > 512 || value % 32) return fail(c, PCT_ERR_ARG, "CTA threads must be 32..512, multiple of 32");
+        c->cta = (int)value;
+        return PCT_OK;
+    case PCT_OPT_MLP_STEP_UM: {
+        if (value < 0 || value > 100000) return fail(c, PCT_ERR_ARG, "MLP step out of range");
+        const int64_t old = c->du_um;
+        c->du_um = value;
+        pct_status s = build_sigma_table(c);
+        if (s != PCT_OK) c->du_um = old;
+        return s;
+    }
+    case PCT_OPT_MEM_CAP_BYTES:
+        if (value < 0) return fail(c, PCT_ERR_ARG, "negative memory cap");
+        c->mem_cap = value;
+        return PCT_OK;
+    case PCT_OPT_TIMING:
+        c->timing = value ? 1 : 0;
+        return PCT_OK;
+    default:
+        return fail(c, PCT_ERR_ARG, "unknown option key");
+    }
+}
+
+pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
+{
+    if (!c || !value) return PCT_ERR_ARG;
+    switch (key) {
+    case PCT_OPT_CTA_THREADS: *value = c->cta; return PCT_OK;
+    case PCT_OPT_MLP_STEP_UM: *value = (int64_t)std::llround(step_mm(c) * 1000.0); return PCT_OK;
+    case PCT_OPT_MEM_CAP_BYTES: *value = c->mem_cap; return PCT_OK;
+    case PCT_OPT_TIMING: *value = c->timing; return PCT_OK;
+    default: return PCT_ERR_ARG;
+    }
+}
+
+pct_status pct_load_histories(pct_ctx* c, int64_t n, const float* const in_xyz[3],
+                              const float* const out_xyz[3], const float* const ang_in[2],
+                              const float* const ang_out[2], const float* gantry_rad,
+                              const float* wepl_mm, int ptrs_on_device)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (n < 0) return fail(c, PCT_ERR_ARG, "negative proton count");
+    DeviceGuard dg(c->device);
+    if (n == 0) {
+        c->n = 0;
+        c->loaded = true;
+        return PCT_OK;
+    }
+    if (!in_xyz || !out_xyz || !ang_in || !ang_out || !gantry_rad || !wepl_mm)
+        return fail(c, PCT_ERR_ARG, "null history pointer");
+    const float* src[H_NF] = {in_xyz[0], in_xyz[1], in_xyz[2], out_xyz[0], out_xyz[1], out_xyz[2],
+                              ang_in[0], ang_in[1], ang_out[0], ang_out[1], gantry_rad, wepl_mm};
+    for (int f = 0; f < H_NF; ++f)
+        if (!src[f]) return fail(c, PCT_ERR_ARG, "null history pointer");
+    const int64_t stride = (n + 31) / 32 * 32;
+    if (stride > c->cap) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c, c->d_hist);
+        dfree(c, c->d_rec);
+        c->d_hist = c->d_rec = nullptr;
+        c->cap = 0;
+        c->n = 0;
+        c->loaded = false;
+        void* p = nullptr;
+        pct_status s = dalloc(c, &p, (size_t)stride * H_NF * sizeof(float), "histories");
+        if (s != PCT_OK) return s;
+        c->d_hist = (float*)p;
+        s = dalloc(c, &p, (size_t)stride * R_NF * sizeof(float), "proton records");
+        if (s != PCT_OK) {
+            dfree(c, c->d_hist);
+            c->d_hist = nullptr;
+            return s;
+        }
+        c->d_rec = (float*)p;
+        c->cap = stride;
+    }
+    c->stride = stride;
+    const cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    for (int f = 0; f < H_NF; ++f) {
+        cudaError_t e = cudaMemcpyAsync(c->d_hist + (size_t)f * stride, src[f], (size_t)n * sizeof(float),
+                                        kind, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "history copy");
+    }
+    if (!ptrs_on_device) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "history copy");
+    }
+    c->n = n;
+    c->loaded = true;
+    return PCT_OK;
+}
+
+pct_status pct_hull_states(pct_ctx* c, int64_t first, int64_t count, float* out)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (first < 0 || count < 0 || first + count > c->n) return fail(c, PCT_ERR_ARG, "proton range out of bounds");
+    if (count > 0 && !out) return fail(c, PCT_ERR_ARG, "null output");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s == PCT_OK) s = prepare(c);
+    if (s != PCT_OK) return s;
+    cudaError_t e = launch_hull_states(launch_of(c), c->d_rec, c->stride, first, count, out);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "hull states");
+}
+
+pct_status pct_mlp(pct_ctx* c, int64_t first, int64_t count, int32_t max_pts, float* out_xyz,
+                   int32_t* out_npts)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (first < 0 || count < 0 || first + count > c->n) return fail(c, PCT_ERR_ARG, "proton range out of bounds");
+    if (max_pts < 2) return fail(c, PCT_ERR_ARG, "max_pts must be >= 2");
+    if (count > 0 && (!out_xyz || !out_npts)) return fail(c, PCT_ERR_ARG, "null output");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s == PCT_OK) s = prepare(c);
+    if (s != PCT_OK) return s;
+    cudaError_t e = launch_mlp_points(launch_of(c), geo_of(c), c->d_rec, c->stride, first, count,
+                                      max_pts, out_xyz, out_npts);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "MLP kernel");
+}
+
+pct_status pct_rows(pct_ctx* c, int64_t first, int64_t count, int32_t max_nnz, int32_t* out_idx,
+                    float* out_len, int32_t* out_nnz)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (first < 0 || count < 0 || first + count > c->n) return fail(c, PCT_ERR_ARG, "proton range out of bounds");
+    if (max_nnz < 0) return fail(c, PCT_ERR_ARG, "negative max_nnz");
+    if (count > 0 && (!out_nnz || (max_nnz > 0 && (!out_idx || !out_len))))
+        return fail(c, PCT_ERR_ARG, "null output");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s == PCT_OK) s = prepare(c);
+    if (s != PCT_OK) return s;
+    cudaError_t e = launch_rows(launch_of(c), geo_of(c), c->d_rec, c->stride, first, count, max_nnz,
+                                out_idx, out_len, out_nnz);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "row kernel");
+}
+
+pct_status pct_forward(pct_ctx* c, const float* x, float* y)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (c->n > 0 && (!x || !y)) return fail(c, PCT_ERR_ARG, "null vector");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s == PCT_OK) s = prepare(c);
+    if (s != PCT_OK) return s;
+    cudaError_t e = launch_forward(launch_of(c), geo_of(c), c->d_rec, c->stride, c->n, x, y);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "forward kernel");
+}
+
+pct_status pct_adjoint(pct_ctx* c, const float* y, float* g)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!g || (c->n > 0 && !y)) return fail(c, PCT_ERR_ARG, "null vector");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s == PCT_OK) s = prepare(c);
+    if (s != PCT_OK) return s;
+    cudaError_t e = cudaMemsetAsync(g, 0, (size_t)c->n_vox * sizeof(float), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint clear");
+    e = launch_adjoint(launch_of(c), geo_of(c), c->d_rec, c->stride, c->n, y, g);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "adjoint kernel");
+}
+
+pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size, float* x)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!x) return fail(c, PCT_ERR_ARG, "null x");
+    if (iters < 0) return fail(c, PCT_ERR_ARG, "negative iteration count");
+    if (block_size < 1) return fail(c, PCT_ERR_ARG, "block size must be >= 1");
+    if (!std::isfinite(lambda)) return fail(c, PCT_ERR_ARG, "non-finite lambda");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s != PCT_OK) return s;
+    if (c->n == 0 || iters == 0) return PCT_OK;
+    if ((s = ensure_acc(c)) != PCT_OK) return s;
+    if ((s = prepare(c)) != PCT_OK) return s;
+    cudaError_t e = cudaMemsetAsync(c->d_acc, 0, (size_t)c->n_vox * sizeof(float2), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "accumulator clear");
+    const Launch L = launch_of(c);
+    const Geo G = geo_of(c);
+    for (int32_t it = 0; it < iters; ++it) {
+        for (int64_t first = 0; first < c->n; first += block_size) {
+            const int64_t count = block_size < c->n - first ? block_size : c->n - first;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (c->timing) {
+                e0 = next_event(c);
+                e1 = next_event(c);
+                if (e0) cudaEventRecord(e0, c->stream);
+            }
+            e = launch_drop_fused(L, G, c->d_rec, c->stride, first, count, x, c->d_acc);
+            if (e != cudaSuccess) return cuda_fail(c, e, "DROP kernel");
+            ++c->fused_launches;
+            if (e1) cudaEventRecord(e1, c->stream);
+            e = launch_drop_apply(L, c->n_vox, x, c->d_acc, lambda);
+            if (e != cudaSuccess) return cuda_fail(c, e, "DROP apply kernel");
+        }
+    }
+    return PCT_OK;
+}
+
+pct_status pct_solve_host(pct_ctx* c, int32_t iters, float lambda, int64_t block_size, float* x_host)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!x_host) return fail(c, PCT_ERR_ARG, "null x");
+    DeviceGuard dg(c->device);
+    if (!c->d_xtmp) {
+        void* p = nullptr;
+        pct_status s = dalloc(c, &p, (size_t)c->n_vox * sizeof(float), "host-solve iterate");
+        if (s != PCT_OK) return s;
+        c->d_xtmp = (float*)p;
+    }
+    const size_t bytes = (size_t)c->n_vox * sizeof(float);
+    cudaError_t e = cudaMemcpyAsync(c->d_xtmp, x_host, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "x upload");
+    pct_status s = pct_solve(c, iters, lambda, block_size, c->d_xtmp);
+    if (s != PCT_OK) return s;
+    e = cudaMemcpyAsync(x_host, c->d_xtmp, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "x download");
+    return pct_synchronize(c);
+}
+
+pct_status pct_synchronize(pct_ctx* c)
+{
+    if (!c) return PCT_ERR_ARG;
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+    unsigned flags = 0;
+    e = cudaMemcpy(&flags, c->d_flags, sizeof flags, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(c, e, "flag read");
+    if (flags) {
+        cudaMemset(c->d_flags, 0, sizeof(unsigned));
+        std::string m = "device check failed:";
+        if (flags & kFlagWalkGuard) m += " voxel walk step bound exceeded;";
+        if (flags & kFlagHullGuard) m += " hull search step bound exceeded;";
+        if (flags & kFlagMlpTable) m += " MLP sample beyond table;";
+        return fail(c, PCT_ERR_DEVICE, m);
+    }
+    return PCT_OK;
+}
+
+pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
+{
+    if (!c || !value) return PCT_ERR_ARG;
+    DeviceGuard dg(c->device);
+    switch (key) {
+    case PCT_STAT_LAUNCHES: *value = (double)c->launches; return PCT_OK;
+    case PCT_STAT_FUSED_LAUNCHES: *value = (double)c->fused_launches; return PCT_OK;
+    case PCT_STAT_FUSED_MS: {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+        double ms = 0.0;
+        for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]) == cudaSuccess) ms += t;
+        }
+        cudaGetLastError();
+        *value = ms;
+        return PCT_OK;
+    }
+    case PCT_STAT_DEVICE_BYTES: *value = (double)c->mem_used; return PCT_OK;
+    case PCT_STAT_N_PROTONS: *value = (double)c->n; return PCT_OK;
+    case PCT_STAT_N_HULL_VOXELS: *value = (double)c->n_hull; return PCT_OK;
+    default: return fail(c, PCT_ERR_ARG, "unknown stat key");
+    }
+}
+
+pct_status pct_reset_stats(pct_ctx* c)
+{
+    if (!c) return PCT_ERR_ARG;
+    c->launches = 0;
+    c->fused_launches = 0;
+    c->ev_used = 0;
+    return PCT_OK;
+}
+
+}  // extern "C"
