@@ -122,14 +122,15 @@ def _pci_id(torch, dev):
 # ----------------------------------------------------------------------------
 FLOP_PER_SAMPLE = 103   # one MLP sample: Sigma2 moments, Highland factor, 2x2 Kalman gain, 2 planes
 FLOP_PER_SEGMENT = 25   # segment set-up of the voxel walk (direction, length, first crossings)
-FLOP_PER_VISIT = 14     # one face crossing + the visit's dot (FMA x2) or scatter product
+FLOP_PER_VISIT = 16     # one face crossing, the dot and norm FMAs, the scatter product
 
 
 def fused_flops(n_valid, mean_pts, mean_nnz):
+    """Algorithmic FP32 flops of one DROP pass over n_valid rows: each row's MLP
+    samples, walk segments and visits once (the scatter reuses the walk)."""
     samples = max(mean_pts - 2.0, 0.0)
     segs = max(mean_pts - 1.0, 0.0)
-    per_pass = samples * FLOP_PER_SAMPLE + segs * FLOP_PER_SEGMENT + mean_nnz * FLOP_PER_VISIT
-    return 2.0 * per_pass * n_valid
+    return (samples * FLOP_PER_SAMPLE + segs * FLOP_PER_SEGMENT + mean_nnz * FLOP_PER_VISIT) * n_valid
 
 
 def _kernel_hash():
@@ -334,7 +335,7 @@ def run_ours(args):
                 "kernel": "k_drop_fused", "avg_launch_ms": avg_launch_s * 1e3,
                 "launches_timed": fused_n,
                 "peak_source": "148 SMs x 128 FP32 lanes x 2 x %g MHz (MEASURED_PEAKS sm_max_mhz)" % sm_mhz,
-                "flops_model": "2 passes x (%.1f MLP samples x %d + %.1f segments x %d + %.1f visits x %d) "
+                "flops_model": "(%.1f MLP samples x %d + %.1f segments x %d + %.1f visits x %d) "
                                "per valid row" % (max(mean_pts - 2, 0), FLOP_PER_SAMPLE,
                                                   max(mean_pts - 1, 0), FLOP_PER_SEGMENT, mean_nnz,
                                                   FLOP_PER_VISIT),

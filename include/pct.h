@@ -62,8 +62,8 @@ typedef struct pct_grid {
 
 /* Keys of pct_set_option / pct_get_option. */
 enum pct_option {
-    /* Threads of one CUDA block of the per-proton kernels: 32..512, multiple
-     * of 32.  Default 256.  Performance only. */
+    /* Threads of one CUDA block of the per-proton kernels (one warp per
+     * proton): 32..256, multiple of 32.  Default 256.  Performance only. */
     PCT_OPT_CTA_THREADS = 1,
     /* MLP sample spacing along the beam depth, in micrometres.  Default: the
      * smallest voxel edge.  Changes A (both the solver and any reference that

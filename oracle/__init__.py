@@ -75,7 +75,7 @@ def _L():
         lib.o_hull_entry.argtypes = [P, P, P, P, ctypes.c_double, P, P]
         lib.o_prepare.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
         lib.o_mlp_points.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int32, P, P]
-        lib.o_rows.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P]
+        lib.o_rows.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, P]
         lib.o_walk.argtypes = [P, P, ctypes.c_int64, P, P, P, ctypes.c_int64, P]
         lib.o_walk.restype = ctypes.c_int64
         lib.o_drop.argtypes = [ctypes.c_int64, ctypes.c_int64, P, P, P, P, ctypes.c_int32,
@@ -203,26 +203,33 @@ def mlp_points(geo: Geometry, hist, max_pts: int):
     return pts, npts
 
 
-def rows(geo: Geometry, hist):
+def rows(geo: Geometry, hist, with_cond: bool = False):
     """Rows of A in path order: (rowptr int64 (n+1,), j int32, chord mm float64, margin (n,)).
 
     A row lists the visits of the MLP polyline (maximal runs inside one voxel)
     in hull voxels, in the order the path meets them; ``margin`` is the
     smallest distance (mm) from a crossing, a turning vertex or the sample-count
     boundary to a voxel face -- rows below 1e-4 mm are near-face cases.
+    With ``with_cond`` a fifth array gives, per row, the largest ratio of
+    segment length to its extent across a crossed face (how much a sideways
+    position error moves a crossing along the path; 1 for a head-on crossing).
     """
     keep, arr, n = _hist_arrays(hist)
     rowptr = np.zeros(n + 1, dtype=np.int64)
     margin = np.zeros(n)
+    cond = np.ones(n)
     lib = _L()
-    lib.o_rows(geo._cp(), geo._mp(), n, arr, _ptr(rowptr), None, None, _ptr(margin))
+    lib.o_rows(geo._cp(), geo._mp(), n, arr, _ptr(rowptr), None, None, _ptr(margin), _ptr(cond))
     np.cumsum(rowptr, out=rowptr)
     nnz = int(rowptr[-1])
     j = np.zeros(max(nnz, 1), dtype=np.int32)
     ln = np.zeros(max(nnz, 1))
-    if lib.o_rows(geo._cp(), geo._mp(), n, arr, _ptr(rowptr), _ptr(j), _ptr(ln), _ptr(margin)) != 0:
+    if lib.o_rows(geo._cp(), geo._mp(), n, arr, _ptr(rowptr), _ptr(j), _ptr(ln), _ptr(margin),
+                  _ptr(cond)) != 0:
         raise RuntimeError("oracle row count changed between passes")
     del keep
+    if with_cond:
+        return rowptr, j[:nnz], ln[:nnz], margin, cond
     return rowptr, j[:nnz], ln[:nnz], margin
 
 
@@ -242,8 +249,10 @@ def csr(rowptr, j, ln, n_vox: int):
     """A as a scipy CSR matrix (m x n_vox) with repeated (i, j) entries summed."""
     import scipy.sparse as sp
     m = rowptr.size - 1
-    A = sp.csr_matrix((np.asarray(ln, dtype=np.float64), np.asarray(j, dtype=np.int64),
-                       np.asarray(rowptr, dtype=np.int64)), shape=(m, n_vox))
+    # copies: scipy would otherwise share the caller's arrays, and summing
+    # duplicates sorts each row in place
+    A = sp.csr_matrix((np.array(ln, dtype=np.float64), np.array(j, dtype=np.int64),
+                       np.array(rowptr, dtype=np.int64)), shape=(m, n_vox))
     A.sum_duplicates()
     A.eliminate_zeros()
     return A
@@ -251,7 +260,7 @@ def csr(rowptr, j, ln, n_vox: int):
 
 def drop(A, b, iters: int, lam: float, block: int, x0) -> np.ndarray:
     """DROP (Sec. IV-B): ``iters`` passes over blocks of ``block`` consecutive rows."""
-    A = A.tocsr()
+    A = A.tocsr(copy=True)
     A.sum_duplicates()
     A.eliminate_zeros()
     rowptr = np.ascontiguousarray(A.indptr, dtype=np.int64)

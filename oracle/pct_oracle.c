@@ -418,7 +418,7 @@ static void o_row_add(o_row *r, const int32_t iv[3], double len)
  * voxel the segment moves into; equal crossing parameters on several axes
  * step all of them at once (no zero-length chord).  Returns the row length. */
 static int64_t o_walk_row(const o_cfg *g, const uint8_t *mask, const double *pts, int64_t np,
-                          int32_t *out_j, double *out_l, int64_t cap, double *margin)
+                          int32_t *out_j, double *out_l, int64_t cap, double *margin, double *cond)
 {
     const double d[3] = {g->dx, g->dy, g->dz};
     const double o[3] = {g->ox, g->oy, g->oz};
@@ -434,8 +434,10 @@ static int64_t o_walk_row(const o_cfg *g, const uint8_t *mask, const double *pts
         const double *A = pts + 3 * k, *B = pts + 3 * k + 3;
         double gA[3], D[3], len2 = 0.0;
         for (int a = 0; a < 3; ++a) {
+            /* both vertices in grid units by the same expression, so that a
+             * segment ends exactly where the next one starts */
             gA[a] = (A[a] - o[a]) / d[a];
-            D[a] = (B[a] - A[a]) / d[a];
+            D[a] = (B[a] - o[a]) / d[a] - gA[a];
             len2 += (B[a] - A[a]) * (B[a] - A[a]);
         }
         double len = sqrt(len2);
@@ -483,6 +485,12 @@ static int64_t o_walk_row(const o_cfg *g, const uint8_t *mask, const double *pts
                 if (tm[a] == tn) {
                     iv[a] += D[a] > 0.0 ? 1 : -1;
                     tm[a] += td[a];
+                    /* path length per unit of travel across the crossed face:
+                     * how far a sideways error moves this crossing */
+                    if (cond) {
+                        double c = len / fabs(D[a] * d[a]);
+                        if (c > *cond) *cond = c;
+                    }
                 } else if (margin) {
                     double m = o_face_dist(A[a] + tn * D[a] * d[a], o[a], d[a]);
                     if (m < *margin) *margin = m;
@@ -500,7 +508,7 @@ static int64_t o_walk_row(const o_cfg *g, const uint8_t *mask, const double *pts
  * lengths are written to rowptr[1..n] (rowptr[0] = 0 is left to the caller's
  * prefix sum); otherwise rowptr must hold the offsets. */
 int o_rows(const o_cfg *g, const uint8_t *mask, int64_t n, const double *const h[12],
-           int64_t *rowptr, int32_t *out_j, double *out_l, double *margin)
+           int64_t *rowptr, int32_t *out_j, double *out_l, double *margin, double *cond)
 {
     int err = 0;
 #pragma omp parallel
@@ -520,18 +528,20 @@ int o_rows(const o_cfg *g, const uint8_t *mask, int64_t n, const double *const h
                 o_state_one(g, mask, h, i, st, &m);
                 np = o_polyline(g, st, ok, pts, cap_pts, &m);
             }
+            double cd = 1.0;
             if (out_j == NULL) {
-                rowptr[i + 1] = o_walk_row(g, mask, pts, np, NULL, NULL, 0, &m);
+                rowptr[i + 1] = o_walk_row(g, mask, pts, np, NULL, NULL, 0, &m, &cd);
             } else {
                 int64_t cap = rowptr[i + 1] - rowptr[i];
                 int64_t got = o_walk_row(g, mask, pts, np, out_j + rowptr[i], out_l + rowptr[i],
-                                         cap, &m);
+                                         cap, &m, &cd);
                 if (got != cap) {
 #pragma omp atomic write
                     err = 1;
                 }
             }
             if (margin) margin[i] = m;
+            if (cond) cond[i] = cd;
         }
         free(pts);
     }
@@ -542,7 +552,7 @@ int o_rows(const o_cfg *g, const uint8_t *mask, int64_t n, const double *const h
 int64_t o_walk(const o_cfg *g, const uint8_t *mask, int64_t np, const double *pts, int32_t *out_j,
                double *out_l, int64_t cap, double *margin)
 {
-    return o_walk_row(g, mask, pts, np, out_j, out_l, cap, margin);
+    return o_walk_row(g, mask, pts, np, out_j, out_l, cap, margin, NULL);
 }
 
 /* ---------------------------------------------------------------------- */

@@ -11,7 +11,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libpct.so")
 SOURCES = ["pct_api.cu", "pct_kernels.cu"]
-HEADERS = ["pct_device.cuh", "pct_internal.h"]
+HEADERS = ["pct_device.cuh", "pct_warp.cuh", "pct_internal.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]

@@ -173,6 +173,10 @@ Geo geo_of(const pct_ctx* c)
     for (int k = 0; k < 6; ++k) G.mc.coef[k] = (float)kCoef200[k];
     G.mc.sig1 = c->d_sig1;
     G.mc.kmax = c->kmax;
+    // a lane range of cmin segments is deeper than the longest chord of a voxel
+    const double diag = std::sqrt((double)c->grid.dx * c->grid.dx + (double)c->grid.dy * c->grid.dy +
+                                  (double)c->grid.dz * c->grid.dz);
+    G.mc.cmin = (int)std::floor(diag / du) + 1;
     G.mask = c->d_mask;
     G.flags = c->d_flags;
     return G;
@@ -329,7 +333,7 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
     DeviceGuard dg(c->device);
     switch (key) {
     case PCT_OPT_CTA_THREADS:
-        if (value < 32 || value > 512 || value % 32) return fail(c, PCT_ERR_ARG, "CTA threads must be 32..512, multiple of 32");
+        if (value < 32 || value > 256 || value % 32) return fail(c, PCT_ERR_ARG, "CTA threads must be 32..256, multiple of 32");
         c->cta = (int)value;
         return PCT_OK;
     case PCT_OPT_MLP_STEP_UM: {
@@ -567,6 +571,7 @@ pct_status pct_synchronize(pct_ctx* c)
         if (flags & kFlagWalkGuard) m += " voxel walk step bound exceeded;";
         if (flags & kFlagHullGuard) m += " hull search step bound exceeded;";
         if (flags & kFlagMlpTable) m += " MLP sample beyond table;";
+        if (flags & kFlagRowSlots) m += " a row too long for pct_rows (nnz reported as -1);";
         return fail(c, PCT_ERR_DEVICE, m);
     }
     return PCT_OK;

@@ -6,8 +6,7 @@
 //      entry/exit states (Gaussian multiple-scattering MLP cited in Sec. I);
 //   2. a 3D voxel walk along the MLP polyline, producing the row a_i as a
 //      sequence of (voxel j, chord a_ij) visits;
-// and hands each visit to a visitor (row dot product, DROP scatter, A x,
-// A^T y, or a debug writer).
+// (pct_warp.cuh), one warp per proton.
 //
 // MLP arithmetic here (FP32, Kalman form):
 //   y1 = R0 y0 + S1 R1^T (R1 S1 R1^T + S2)^-1 (y2 - R1 R0 y0),
@@ -32,6 +31,7 @@ constexpr float kX0 = 36.08f;  // cm
 constexpr unsigned kFlagWalkGuard = 1u;   // a segment walk exceeded its step bound
 constexpr unsigned kFlagHullGuard = 2u;   // a hull search exceeded its step bound
 constexpr unsigned kFlagMlpTable = 4u;    // MLP sample index beyond the S1 table
+constexpr unsigned kFlagRowSlots = 8u;    // a debug row had more runs per lane than its slots
 
 struct GridC {
     int nx, ny, nz;
@@ -45,6 +45,7 @@ struct MlpC {
     float coef[6];        // 1/(beta^2 p^2) = sum coef[k] u^k, MeV^-2, u in cm
     const float4* sig1;   // sig1[k] = Sigma(0, k*du): (S00, S01, S11, 0), cm / rad
     int kmax;             // last valid index of sig1
+    int cmin;             // fewest segments per lane range whose depth exceeds a voxel diagonal
 };
 
 // Per-proton record written once per call by the prepare kernel (SoA).
@@ -136,7 +137,9 @@ __device__ __forceinline__ void mlp_offset(const Path& P, const MlpC& mc, int k,
     q0 = fmaf(q0, W, P.c2[0]);
     q1 = fmaf(q1, W, P.c2[0] * (1.f / 2.f));
     q2 = fmaf(q2, W, P.c2[0] * (1.f / 3.f));
-    const float lf = fmaf(0.038f, logf(W * (1.f / kX0)), 1.f);
+    // Highland factor: an absolute error of 1e-6 in the logarithm moves it by
+    // 4e-8 relative, so the hardware log2 is accurate enough here
+    const float lf = fmaf(0.038f * 0.69314718f, __log2f(W * (1.f / kX0)), 1.f);
     const float pre = (kE0 * kE0 / kX0) * lf * lf * W;
     const float T11 = pre * q0;             // Sigma2 entries (cm, rad)
     const float T01 = pre * W * q1;
@@ -146,7 +149,7 @@ __device__ __forceinline__ void mlp_offset(const Path& P, const MlpC& mc, int k,
     const float M11 = s1.z + T11;
     const float g0 = fmaf(W, s1.y, s1.x);
     const float g1 = s1.y;
-    const float rdet = 1.f / fmaf(M00, M11, -M01 * M01);
+    const float rdet = __frcp_rn(fmaf(M00, M11, -M01 * M01));
     const float G0 = fmaf(g0, M11, -g1 * M01) * rdet;           // dimensionless
     const float G1 = fmaf(g1, M00, -g0 * M01) * rdet * 10.f;    // mm per rad
     dt = fmaf(w_mm, P.th0, fmaf(G0, P.d0t, G1 * P.d1t));
@@ -184,221 +187,57 @@ __device__ __forceinline__ int start_index(float a, float dir)
     return k;
 }
 
-// Walk the MLP polyline of P.  For each maximal run of the path inside one
-// voxel, with positive length, calls vis.visit(ix, iy, iz, chord_mm).
-template <class V>
-__device__ __forceinline__ void walk_path(const Path& P, const MlpC& mc, const GridC& g,
-                                          unsigned* flags, V& vis)
-{
-    float ax = P.px, ay = P.py, az = P.pz;
-    float bx, by, bz;
-    path_point(P, mc, g, 1, bx, by, bz);
-    int ix = start_index(ax, bx - ax);
-    int iy = start_index(ay, by - ay);
-    int iz = start_index(az, bz - az);
-    float run = 0.f;
-    const float INF = __int_as_float(0x7f800000);
-    for (int k = 1; k <= P.nseg; ++k) {
-        if (k > 1) path_point(P, mc, g, k, bx, by, bz);
-        const float Dx = bx - ax, Dy = by - ay, Dz = bz - az;
-        const float ex = Dx * g.dx, ey = Dy * g.dy, ez = Dz * g.dz;
-        const float len = sqrtf(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
-        const int sx = Dx > 0.f ? 1 : -1, sy = Dy > 0.f ? 1 : -1, sz = Dz > 0.f ? 1 : -1;
-        const float rx = 1.f / Dx, ry = 1.f / Dy, rz = 1.f / Dz;
-        float tmx = Dx > 0.f ? (float)(ix + 1) - ax : (Dx < 0.f ? (float)ix - ax : INF);
-        float tmy = Dy > 0.f ? (float)(iy + 1) - ay : (Dy < 0.f ? (float)iy - ay : INF);
-        float tmz = Dz > 0.f ? (float)(iz + 1) - az : (Dz < 0.f ? (float)iz - az : INF);
-        if (Dx != 0.f) tmx *= rx;
-        if (Dy != 0.f) tmy *= ry;
-        if (Dz != 0.f) tmz *= rz;
-        const float tdx = fabsf(rx), tdy = fabsf(ry), tdz = fabsf(rz);
-        // a segment crosses at most |D|_1 + 3 faces
-        const int guard = (int)(fabsf(Dx) + fabsf(Dy) + fabsf(Dz)) + 4;
-        float t = 0.f;
-        int n = 0;
-        for (;;) {
-            const float tn = fminf(tmx, fminf(tmy, tmz));
-            if (!(tn < 1.f)) {
-                run = fmaf(1.f - t, len, run);
-                break;
-            }
-            const float tc = fmaxf(tn, t);
-            run = fmaf(tc - t, len, run);
-            if (run > 0.f) vis.visit(ix, iy, iz, run);
-            run = 0.f;
-            if (tmx == tn) { ix += sx; tmx += tdx; }
-            if (tmy == tn) { iy += sy; tmy += tdy; }
-            if (tmz == tn) { iz += sz; tmz += tdz; }
-            t = tc;
-            if (++n > guard) {
-                atomicOr(flags, kFlagWalkGuard);
-                break;
-            }
-        }
-        ax = bx;
-        ay = by;
-        az = bz;
-    }
-    if (run > 0.f) vis.visit(ix, iy, iz, run);
-}
-
 __device__ __forceinline__ bool in_grid(const GridC& g, int ix, int iy, int iz)
 {
     return (unsigned)ix < (unsigned)g.nx && (unsigned)iy < (unsigned)g.ny &&
            (unsigned)iz < (unsigned)g.nz;
 }
 
-__device__ __forceinline__ int64_t lin(const GridC& g, int ix, int iy, int iz)
+// Linear voxel index (grids hold fewer than 2^31 voxels).
+__device__ __forceinline__ int lin(const GridC& g, int ix, int iy, int iz)
 {
-    return ix + (int64_t)g.nx * (iy + (int64_t)g.ny * iz);
+    return ix + g.nx * (iy + g.ny * iz);
 }
-
-// ---------------------------------------------------------------------------
-// Visitors.  The hull-mask byte of a visit is loaded when the visit is emitted
-// and consumed at the next one ("pending" visit), so that its latency overlaps
-// the MLP arithmetic of the following segment instead of stalling the thread.
-// ---------------------------------------------------------------------------
-
-// s = a_i . x and q = ||a_i||^2 over hull voxels.
-struct DotVisitor {
-    const GridC* g;
-    const uint8_t* __restrict__ mask;
-    const float* __restrict__ x;
-    float s, q;
-    float pl, px;
-    uint8_t pm;
-    __device__ __forceinline__ void visit(int ix, int iy, int iz, float l)
-    {
-        uint8_t m = 0;
-        float xv = 0.f;
-        if (in_grid(*g, ix, iy, iz)) {
-            const int64_t j = lin(*g, ix, iy, iz);
-            m = __ldg(mask + j);
-            xv = __ldg(x + j);
-        }
-        if (pm) {
-            s = fmaf(pl, px, s);
-            q = fmaf(pl, pl, q);
-        }
-        pm = m;
-        pl = l;
-        px = xv;
-    }
-    __device__ __forceinline__ void finish()
-    {
-        if (pm) {
-            s = fmaf(pl, px, s);
-            q = fmaf(pl, pl, q);
-        }
-        pm = 0;
-    }
-};
-
-// DROP scatter: acc[j] += (a_ij * r, 1) over hull voxels.
-struct ScatterVisitor {
-    const GridC* g;
-    const uint8_t* __restrict__ mask;
-    float2* acc;
-    float r;
-    int64_t pj;
-    float pl;
-    uint8_t pm;
-    __device__ __forceinline__ void visit(int ix, int iy, int iz, float l)
-    {
-        uint8_t m = 0;
-        int64_t j = 0;
-        if (in_grid(*g, ix, iy, iz)) {
-            j = lin(*g, ix, iy, iz);
-            m = __ldg(mask + j);
-        }
-        if (pm) atomicAdd(acc + pj, make_float2(pl * r, 1.f));
-        pm = m;
-        pj = j;
-        pl = l;
-    }
-    __device__ __forceinline__ void finish()
-    {
-        if (pm) atomicAdd(acc + pj, make_float2(pl * r, 1.f));
-        pm = 0;
-    }
-};
-
-// A^T y scatter: g[j] += a_ij * y_i over hull voxels.
-struct AdjointVisitor {
-    const GridC* g;
-    const uint8_t* __restrict__ mask;
-    float* out;
-    float yi;
-    int64_t pj;
-    float pl;
-    uint8_t pm;
-    __device__ __forceinline__ void visit(int ix, int iy, int iz, float l)
-    {
-        uint8_t m = 0;
-        int64_t j = 0;
-        if (in_grid(*g, ix, iy, iz)) {
-            j = lin(*g, ix, iy, iz);
-            m = __ldg(mask + j);
-        }
-        if (pm) atomicAdd(out + pj, pl * yi);
-        pm = m;
-        pj = j;
-        pl = l;
-    }
-    __device__ __forceinline__ void finish()
-    {
-        if (pm) atomicAdd(out + pj, pl * yi);
-        pm = 0;
-    }
-};
-
-// Debug: write the row (hull visits in path order).
-struct RowWriter {
-    const GridC* g;
-    const uint8_t* __restrict__ mask;
-    int32_t* idx;
-    float* len;
-    int32_t cap;
-    int32_t n;
-    __device__ __forceinline__ void visit(int ix, int iy, int iz, float l)
-    {
-        if (!in_grid(*g, ix, iy, iz)) return;
-        const int64_t j = lin(*g, ix, iy, iz);
-        if (!__ldg(mask + j)) return;
-        if (n < cap) {
-            idx[n] = (int32_t)j;
-            len[n] = l;
-        }
-        ++n;
-    }
-    __device__ __forceinline__ void finish() {}
-};
 
 // ---------------------------------------------------------------------------
 // Hull entry along a straight tracker line (reading: the paper names no hull
 // rule; the path starts where the line first enters a hull voxel).
 // Line p(s) = T + s D (grid units per mm of depth), s in [0, S].
 // ---------------------------------------------------------------------------
+// On a hit, (axis, face) name the grid plane the line crosses into the hull
+// voxel (face in grid units along axis); axis = -1 when the line starts inside
+// that voxel (s_hit = 0).  The caller re-evaluates the crossing parameter from
+// them in FP64: for a line nearly parallel to the plane the FP32 parameter is
+// ill-conditioned.
 __device__ __forceinline__ bool hull_entry(const GridC& g, const uint8_t* __restrict__ mask,
                                            float Tx, float Ty, float Tz, float Dx, float Dy,
-                                           float Dz, float S, unsigned* flags, float& s_hit)
+                                           float Dz, float S, unsigned* flags, float& s_hit,
+                                           int& axis, int& face)
 {
     float s_lo = 0.f, s_hi = S;
     const float T[3] = {Tx, Ty, Tz};
     const float D[3] = {Dx, Dy, Dz};
     const int n[3] = {g.nx, g.ny, g.nz};
+    axis = -1;
+    face = 0;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (D[a] == 0.f) {
             if (T[a] < 0.f || T[a] >= (float)n[a]) return false;
         } else {
             float s1 = (0.f - T[a]) / D[a], s2 = ((float)n[a] - T[a]) / D[a];
+            int f1 = 0;
             if (s1 > s2) {
                 const float tmp = s1;
                 s1 = s2;
                 s2 = tmp;
+                f1 = n[a];
             }
-            s_lo = fmaxf(s_lo, s1);
+            if (s1 > s_lo) {
+                s_lo = s1;
+                axis = a;
+                face = f1;
+            }
             s_hi = fminf(s_hi, s2);
         }
     }
@@ -432,7 +271,11 @@ __device__ __forceinline__ bool hull_entry(const GridC& g, const uint8_t* __rest
         if (!(s_next < s_hi)) return false;
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            if (tm[a] == s_next) iv[a] += D[a] > 0.f ? 1 : -1;
+            if (tm[a] == s_next) {
+                axis = a;
+                face = D[a] > 0.f ? iv[a] + 1 : iv[a];
+                iv[a] += D[a] > 0.f ? 1 : -1;
+            }
         s_cur = s_next;
         if ((unsigned)iv[0] >= (unsigned)g.nx || (unsigned)iv[1] >= (unsigned)g.ny ||
             (unsigned)iv[2] >= (unsigned)g.nz)

@@ -4,6 +4,7 @@
 // Sec. I) and recompute the proton's row of A from its record: MLP samples,
 // then the voxel walk (pct_device.cuh).  None of them stores A.
 #include "pct_internal.h"
+#include "pct_warp.cuh"
 
 namespace pct {
 
@@ -21,6 +22,17 @@ inline unsigned grid_for(int64_t n, int cta)
 // beam frame of its gantry angle, follow both straight tracker lines to the
 // hull, and store the entry/exit states the MLP starts from.
 // ---------------------------------------------------------------------------
+// Crossing parameter (mm of depth) of the lab line p(s) = T + s D with the grid
+// plane `face` of `axis`, in FP64.
+__device__ __forceinline__ double plane_crossing(const GridC& g, const double T[3], const double D[3],
+                                                 int axis, int face)
+{
+    if (axis < 0) return 0.0;
+    const double o = axis == 0 ? (double)g.ox : (axis == 1 ? (double)g.oy : (double)g.oz);
+    const double d = axis == 0 ? (double)g.dx : (axis == 1 ? (double)g.dy : (double)g.dz);
+    return (fma((double)face, d, o) - T[axis]) / D[axis];
+}
+
 __global__ void __launch_bounds__(kMaxCta)
 k_prepare(GridC g, const uint8_t* __restrict__ mask, unsigned* flags, const float* __restrict__ h,
           int64_t stride, int64_t first, int64_t count, float* __restrict__ rec, float Lmax)
@@ -35,39 +47,51 @@ k_prepare(GridC g, const uint8_t* __restrict__ mask, unsigned* flags, const floa
     const float phi = h[H_PHI * stride + i], wepl = h[H_WEPL * stride + i];
     float s, c;
     sincosf(phi, &s, &c);
-    const float ua = fmaf(xi, c, yi * s), ta = fmaf(-xi, s, yi * c), va = zi;
-    const float ub = fmaf(xo, c, yo * s), tb = fmaf(-xo, s, yo * c), vb = zo;
+    const float ua = fmaf(xi, c, yi * s), ub = fmaf(xo, c, yo * s);
     const float tti = tanf(thi), tpi = tanf(psi), tto = tanf(tho), tpo = tanf(pso);
-    bool ok = isfinite(ua) && isfinite(ub) && isfinite(ta) && isfinite(tb) && isfinite(va) &&
-              isfinite(vb) && isfinite(tti) && isfinite(tpi) && isfinite(tto) && isfinite(tpo) &&
-              ub > ua;
+    bool ok = isfinite(xi) && isfinite(yi) && isfinite(zi) && isfinite(xo) && isfinite(yo) &&
+              isfinite(zo) && isfinite(ua) && isfinite(ub) && isfinite(tti) && isfinite(tpi) &&
+              isfinite(tto) && isfinite(tpo) && ub > ua;
     const float S = ub - ua;
-    // straight lines in grid units per mm of depth
+    // FP32 search of the first hull voxel along each straight tracker line
+    // (grid units per mm of depth)
     const float Tix = (xi - g.ox) * g.idx, Tiy = (yi - g.oy) * g.idy, Tiz = (zi - g.oz) * g.idz;
     const float Dix = fmaf(-tti, s, c) * g.idx, Diy = fmaf(tti, c, s) * g.idy, Diz = tpi * g.idz;
     const float Tox = (xo - g.ox) * g.idx, Toy = (yo - g.oy) * g.idy, Toz = (zo - g.oz) * g.idz;
     const float Dox = -fmaf(-tto, s, c) * g.idx, Doy = -fmaf(tto, c, s) * g.idy, Doz = -tpo * g.idz;
     float s_in = 0.f, s_out = 0.f;
-    if (ok) ok = hull_entry(g, mask, Tix, Tiy, Tiz, Dix, Diy, Diz, S, flags, s_in);
-    if (ok) ok = hull_entry(g, mask, Tox, Toy, Toz, Dox, Doy, Doz, S, flags, s_out);
-    const float u_in = ua + s_in, u_out = ub - s_out;
-    const float L = u_out - u_in;
-    ok = ok && L > 0.f && L <= Lmax;
-    rec[R_C * stride + i] = c;
-    rec[R_S * stride + i] = s;
-    rec[R_UIN * stride + i] = u_in;
-    rec[R_L * stride + i] = ok ? L : 0.f;
-    rec[R_T0 * stride + i] = fmaf(tti, s_in, ta);
+    int ax_in = -1, f_in = 0, ax_out = -1, f_out = 0;
+    if (ok) ok = hull_entry(g, mask, Tix, Tiy, Tiz, Dix, Diy, Diz, S, flags, s_in, ax_in, f_in);
+    if (ok) ok = hull_entry(g, mask, Tox, Toy, Toz, Dox, Doy, Doz, S, flags, s_out, ax_out, f_out);
+    // the record, evaluated once in FP64 from the raw inputs and the crossed planes
+    double sd, cd;
+    sincos((double)phi, &sd, &cd);
+    const double ti = tan((double)thi), pi = tan((double)psi), to = tan((double)tho), po = tan((double)pso);
+    const double Ti[3] = {xi, yi, zi}, To[3] = {xo, yo, zo};
+    const double Di[3] = {fma(-ti, sd, cd), fma(ti, cd, sd), pi};
+    const double Do[3] = {-fma(-to, sd, cd), -fma(to, cd, sd), -po};
+    const double si = ok ? plane_crossing(g, Ti, Di, ax_in, f_in) : 0.0;
+    const double so = ok ? plane_crossing(g, To, Do, ax_out, f_out) : 0.0;
+    const double uad = fma((double)xi, cd, (double)yi * sd), ubd = fma((double)xo, cd, (double)yo * sd);
+    const double tad = fma(-(double)xi, sd, (double)yi * cd), tbd = fma(-(double)xo, sd, (double)yo * cd);
+    const double u_in = uad + si, u_out = ubd - so;
+    const double L = u_out - u_in;
+    ok = ok && L > 0.0 && L <= (double)Lmax;
+    rec[R_C * stride + i] = (float)cd;
+    rec[R_S * stride + i] = (float)sd;
+    rec[R_UIN * stride + i] = (float)u_in;
+    rec[R_L * stride + i] = ok ? (float)L : 0.f;
+    rec[R_T0 * stride + i] = (float)fma(ti, si, tad);
     rec[R_TH0 * stride + i] = thi;
-    rec[R_V0 * stride + i] = fmaf(tpi, s_in, va);
+    rec[R_V0 * stride + i] = (float)fma(pi, si, (double)zi);
     rec[R_PS0 * stride + i] = psi;
-    rec[R_T2 * stride + i] = fmaf(-tto, s_out, tb);
+    rec[R_T2 * stride + i] = (float)fma(-to, so, tbd);
     rec[R_TH2 * stride + i] = tho;
-    rec[R_V2 * stride + i] = fmaf(-tpo, s_out, vb);
+    rec[R_V2 * stride + i] = (float)fma(-po, so, (double)zo);
     rec[R_PS2 * stride + i] = pso;
-    rec[R_PX * stride + i] = fmaf(s_in, Dix, Tix);
-    rec[R_PY * stride + i] = fmaf(s_in, Diy, Tiy);
-    rec[R_PZ * stride + i] = fmaf(s_in, Diz, Tiz);
+    rec[R_PX * stride + i] = (float)((fma(si, Di[0], Ti[0]) - (double)g.ox) / (double)g.dx);
+    rec[R_PY * stride + i] = (float)((fma(si, Di[1], Ti[1]) - (double)g.oy) / (double)g.dy);
+    rec[R_PZ * stride + i] = (float)((fma(si, Di[2], Ti[2]) - (double)g.oz) / (double)g.dz);
     rec[R_B * stride + i] = wepl;
 }
 
@@ -118,78 +142,129 @@ k_mlp_points(GridC g, MlpC mc, RecView rv, int64_t first, int64_t count, int32_t
     }
 }
 
-// Rows of A in path order (debug / parity).
+// Runs a lane can keep in shared memory: DROP / adjoint passes, and the debug
+// row writer (which must not fall back).
+constexpr int kRunSlots = 24;
+// warp-per-proton kernels: at most 256 threads per CTA, 64 registers per thread
+constexpr int kWarpCta = 256;
+constexpr int kWarpCtaMin = 4;
+constexpr int kRowSlots = 64;
+
+__device__ __forceinline__ RunSlots warp_slots(unsigned char* smem, int rl)
+{
+    const int warp = threadIdx.x >> 5;
+    unsigned char* base = smem + (size_t)warp * rl * kWarp * 8;
+    return RunSlots{(int*)base, (float*)(base + (size_t)rl * kWarp * 4)};
+}
+
+// Rows of A in path order (debug / parity), one warp per proton.
 __global__ void __launch_bounds__(kMaxCta)
 k_rows(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
        int64_t first, int64_t count, int32_t max_nnz, int32_t* __restrict__ idx,
        float* __restrict__ len, int32_t* __restrict__ nnz)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    extern __shared__ unsigned char smem[];
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (t >= count) return;
     Path P;
     if (!load_path(rv, first + t, mc, P)) {
-        nnz[t] = 0;
+        if (lane == 0) nnz[t] = 0;
         return;
     }
-    RowWriter w{&g, mask, idx + (int64_t)t * max_nnz, len + (int64_t)t * max_nnz, max_nnz, 0};
-    walk_path(P, mc, g, flags, w);
-    nnz[t] = w.n;
+    const RunSlots slots = warp_slots(smem, kRowSlots);
+    LaneWalk w;
+    float s, q;
+    warp_walk<kRowSlots, false>(P, mc, g, mask, nullptr, flags, slots, mc.cmin, w, s, q);
+    const bool over = __any_sync(0xffffffffu, w.n > kRowSlots);
+    if (over) {
+        if (lane == 0) {
+            nnz[t] = -1;
+            atomicOr(flags, kFlagRowSlots);
+        }
+        return;
+    }
+    int mine = (w.k0 < w.k1) ? w.n - ((w.merged_prev && w.head_in) ? 1 : 0) : 0;
+    int off = mine;
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, off, kWarp - 1);
+    off -= mine;
+    int32_t* oi = idx + t * (int64_t)max_nnz;
+    float* ol = len + t * (int64_t)max_nnz;
+    replay_runs<kRowSlots>(P, mc, g, mask, flags, slots, w, [&](int j, float l) {
+        if (off < max_nnz) {
+            oi[off] = j;
+            ol[off] = l;
+        }
+        ++off;
+    });
+    if (lane == 0) nnz[t] = total;
 }
 
-// y = A x (a10): one row per thread, no atomics.
-__global__ void __launch_bounds__(kMaxCta)
+// y = A x (a10), one warp per row, no atomics.
+__global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_forward(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
           int64_t n, const float* __restrict__ x, float* __restrict__ y)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    extern __shared__ unsigned char smem[];
+    const int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
     Path P;
     if (!load_path(rv, i, mc, P)) {
-        y[i] = 0.f;
+        if ((threadIdx.x & 31) == 0) y[i] = 0.f;
         return;
     }
-    DotVisitor d{&g, mask, x, 0.f, 0.f, 0.f, 0.f, 0};
-    walk_path(P, mc, g, flags, d);
-    d.finish();
-    y[i] = d.s;
+    LaneWalk w;
+    float s, q;
+    warp_walk<0, true>(P, mc, g, mask, x, flags, warp_slots(smem, 0), mc.cmin, w, s, q);
+    if ((threadIdx.x & 31) == 0) y[i] = s;
 }
 
-// g = A^T y (a10): one row per thread, scatter by FP32 atomics.
-__global__ void __launch_bounds__(kMaxCta)
+// g = A^T y (a10), one warp per row, scatter by FP32 atomics.
+__global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
           int64_t n, const float* __restrict__ y, float* gout)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    extern __shared__ unsigned char smem[];
+    const int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
+    const float yi = __ldg(y + i);
+    if (yi == 0.f) return;
     Path P;
     if (!load_path(rv, i, mc, P)) return;
-    const float yi = y[i];
-    if (yi == 0.f) return;
-    AdjointVisitor a{&g, mask, gout, yi, 0, 0.f, 0};
-    walk_path(P, mc, g, flags, a);
-    a.finish();
+    const RunSlots slots = warp_slots(smem, kRunSlots);
+    LaneWalk w;
+    float s, q;
+    warp_walk<kRunSlots, false>(P, mc, g, mask, nullptr, flags, slots, mc.cmin, w, s, q);
+    replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
+                           [&](int j, float l) { atomicAdd(gout + j, l * yi); });
 }
 
-// DROP block step (a3-a6 fused): per proton of the block, with x frozen,
-//   r_i = (b_i - a_i.x) / ||a_i||^2, then acc[j] += (a_ij r_i, 1) on its row.
-// The row is walked twice (dot, then scatter) instead of being stored.
-__global__ void __launch_bounds__(kMaxCta)
+// DROP block step (a3-a6 fused), one warp per proton of the block, x frozen:
+//   r_i = (b_i - a_i.x) / ||a_i||^2, then acc[j] += (a_ij r_i, 1) over its row.
+// The row is walked once; the scatter replays the runs kept in shared memory.
+__global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
              int64_t first, int64_t count, const float* __restrict__ x, float2* acc)
 {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    extern __shared__ unsigned char smem[];
+    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (t >= count) return;
     const int64_t i = first + t;
     Path P;
     if (!load_path(rv, i, mc, P)) return;
-    DotVisitor d{&g, mask, x, 0.f, 0.f, 0.f, 0.f, 0};
-    walk_path(P, mc, g, flags, d);
-    d.finish();
-    if (!(d.q > 0.f)) return;
-    const float r = (rv.get(R_B, i) - d.s) / d.q;
-    ScatterVisitor sc{&g, mask, acc, r, 0, 0.f, 0};
-    walk_path(P, mc, g, flags, sc);
-    sc.finish();
+    const RunSlots slots = warp_slots(smem, kRunSlots);
+    LaneWalk w;
+    float s, q;
+    warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
+    if (!(q > 0.f)) return;
+    const float r = (rv.get(R_B, i) - s) / q;
+    replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
+                           [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
 }
 
 // DROP block apply (a7): x_j += lambda * num_j / s_j where the block touched
@@ -246,14 +321,36 @@ cudaError_t launch_mlp_points(const Launch& L, const Geo& G, const float* rec, i
     PCT_LAUNCH_TAIL(L);
 }
 
+inline unsigned warp_grid(int64_t n, int cta)
+{
+    const int wpc = cta / kWarp;
+    return (unsigned)((n + wpc - 1) / wpc);
+}
+
+inline size_t slot_bytes(int cta, int rl)
+{
+    return (size_t)(cta / kWarp) * rl * kWarp * 8;
+}
+
+template <class K>
+cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 cudaError_t launch_rows(const Launch& L, const Geo& G, const float* rec, int64_t stride,
                         int64_t first, int64_t count, int32_t max_nnz, int32_t* out_idx,
                         float* out_len, int32_t* out_nnz)
 {
     if (count <= 0) return cudaSuccess;
-    k_rows<<<grid_for(count, L.cta), L.cta, 0, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
-                                                            G.flags, first, count, max_nnz, out_idx,
-                                                            out_len, out_nnz);
+    const int cta = 64;   // 2 warps: the row writer keeps 64 slots per lane
+    const size_t sm = slot_bytes(cta, kRowSlots);
+    cudaError_t e = allow_smem(k_rows, sm);
+    if (e != cudaSuccess) return e;
+    k_rows<<<warp_grid(count, cta), cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
+                                                         G.flags, first, count, max_nnz, out_idx,
+                                                         out_len, out_nnz);
     PCT_LAUNCH_TAIL(L);
 }
 
@@ -261,8 +358,8 @@ cudaError_t launch_forward(const Launch& L, const Geo& G, const float* rec, int6
                            int64_t n, const float* x, float* y)
 {
     if (n <= 0) return cudaSuccess;
-    k_forward<<<grid_for(n, L.cta), L.cta, 0, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
-                                                          G.flags, n, x, y);
+    k_forward<<<warp_grid(n, L.cta), L.cta, 0, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
+                                                           G.flags, n, x, y);
     PCT_LAUNCH_TAIL(L);
 }
 
@@ -270,8 +367,11 @@ cudaError_t launch_adjoint(const Launch& L, const Geo& G, const float* rec, int6
                            int64_t n, const float* y, float* g_out)
 {
     if (n <= 0) return cudaSuccess;
-    k_adjoint<<<grid_for(n, L.cta), L.cta, 0, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
-                                                          G.flags, n, y, g_out);
+    const size_t sm = slot_bytes(L.cta, kRunSlots);
+    cudaError_t e = allow_smem(k_adjoint, sm);
+    if (e != cudaSuccess) return e;
+    k_adjoint<<<warp_grid(n, L.cta), L.cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
+                                                            G.flags, n, y, g_out);
     PCT_LAUNCH_TAIL(L);
 }
 
@@ -279,7 +379,10 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
                               int64_t first, int64_t count, const float* x, float2* acc)
 {
     if (count <= 0) return cudaSuccess;
-    k_drop_fused<<<grid_for(count, L.cta), L.cta, 0, L.stream>>>(
+    const size_t sm = slot_bytes(L.cta, kRunSlots);
+    cudaError_t e = allow_smem(k_drop_fused, sm);
+    if (e != cudaSuccess) return e;
+    k_drop_fused<<<warp_grid(count, L.cta), L.cta, sm, L.stream>>>(
         G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, first, count, x, acc);
     PCT_LAUNCH_TAIL(L);
 }

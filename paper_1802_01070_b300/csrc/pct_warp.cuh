@@ -1,0 +1,322 @@
+// pct_warp.cuh -- one warp per proton: the row of A of one proton computed by
+// 32 lanes cooperating (arXiv:1802.01070 maps one proton to one thread; on
+// sm_103a a proton is mapped to one warp so that the lanes run in lockstep).
+//
+// The proton's polyline segments 1..nseg are cut into contiguous lane ranges of
+// C segments (C >= cmin, the smallest count whose depth C*du exceeds a voxel
+// diagonal).  Lane l computes the MLP points l*C .. (l+1)*C -- the same number
+// of samples on every lane -- and walks its range.  Because a range is longer
+// than any chord of a voxel, a run of the path inside one voxel can span at most
+// two neighbouring lanes (the tail of lane l-1 and the head of lane l); one
+// shuffle repairs the squared norm (+2ab) and decides which lane owns such a run
+// for the DROP count and scatter.
+//
+// Pass 1 (walk): every lane stores its hull runs (voxel, chord) in shared
+// memory, accumulates s = a_i.x and q = ||a_i||^2 and records its first and last
+// raw run.  Later passes replay the stored runs instead of recomputing the MLP
+// and the walk; a lane with more runs than its slots re-walks its range.
+#pragma once
+
+#include "pct_device.cuh"
+
+namespace pct {
+
+constexpr int kWarp = 32;
+
+// Per-warp shared-memory slots of stored runs: j[e * 32 + lane], l[e * 32 + lane].
+struct RunSlots {
+    int* j;
+    float* l;
+};
+
+
+// End points of a lane range: the lane computes its first point k0 and takes
+// its last point k1 from the next lane (whose first point it is), so that the
+// vertex two lanes share is the same float triple on both.
+struct RangeEnds {
+    float ax, ay, az;   // point k0
+    float ex, ey, ez;   // point k1
+};
+
+__device__ __forceinline__ RangeEnds range_ends(const Path& P, const MlpC& mc, const GridC& g,
+                                                int k0, int k1)
+{
+    RangeEnds r;
+    path_point(P, mc, g, k0, r.ax, r.ay, r.az);   // k0 >= nseg gives the exit point
+    const unsigned full = 0xffffffffu;
+    r.ex = __shfl_down_sync(full, r.ax, 1);
+    r.ey = __shfl_down_sync(full, r.ay, 1);
+    r.ez = __shfl_down_sync(full, r.az, 1);
+    if ((threadIdx.x & (kWarp - 1)) == kWarp - 1) path_point(P, mc, g, k1, r.ex, r.ey, r.ez);
+    return r;
+}
+
+struct LaneWalk {
+    int k0, k1;          // points k0..k1 of this lane (inactive when k0 >= k1)
+    RangeEnds ends;
+    int n;               // hull runs met (stored while n <= RL)
+    bool any;            // at least one raw run
+    int head_j, tail_j;  // first / last raw run (voxel index or -1 outside the grid)
+    float head_l, tail_l;
+    bool head_in, tail_in;
+    float s, q;          // partial a_i.x and ||a_i||^2 of the lane's runs
+    bool merged_prev;    // head continues the previous lane's tail (same voxel)
+    bool next_merges;    // tail continues into the next lane's head
+    float next_head_l;
+};
+
+// Walk the points k0..k1 of P (ends given); calls on_run(ix, iy, iz, chord) for
+// each maximal run of the path inside one voxel (positive chord), in path order.
+template <class F>
+__device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const GridC& g,
+                                            unsigned* flags, int k0, int k1, const RangeEnds& re,
+                                            F& on_run)
+{
+    float ax = re.ax, ay = re.ay, az = re.az, bx, by, bz;
+    if (k0 + 1 == k1) {
+        bx = re.ex;
+        by = re.ey;
+        bz = re.ez;
+    } else {
+        path_point(P, mc, g, k0 + 1, bx, by, bz);
+    }
+    int ix = start_index(ax, bx - ax);
+    int iy = start_index(ay, by - ay);
+    int iz = start_index(az, bz - az);
+    float run = 0.f;
+    const float INF = __int_as_float(0x7f800000);
+    for (int k = k0 + 1; k <= k1; ++k) {
+        if (k > k0 + 1) {
+            if (k == k1) {
+                bx = re.ex;
+                by = re.ey;
+                bz = re.ez;
+            } else {
+                path_point(P, mc, g, k, bx, by, bz);
+            }
+        }
+        const float Dx = bx - ax, Dy = by - ay, Dz = bz - az;
+        const float ex = Dx * g.dx, ey = Dy * g.dy, ez = Dz * g.dz;
+        const float len = __fsqrt_rn(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+        const int sx = Dx > 0.f ? 1 : -1, sy = Dy > 0.f ? 1 : -1, sz = Dz > 0.f ? 1 : -1;
+        const float rx = __frcp_rn(Dx), ry = __frcp_rn(Dy), rz = __frcp_rn(Dz);
+        float tmx = Dx > 0.f ? (float)(ix + 1) - ax : (Dx < 0.f ? (float)ix - ax : INF);
+        float tmy = Dy > 0.f ? (float)(iy + 1) - ay : (Dy < 0.f ? (float)iy - ay : INF);
+        float tmz = Dz > 0.f ? (float)(iz + 1) - az : (Dz < 0.f ? (float)iz - az : INF);
+        if (Dx != 0.f) tmx *= rx;
+        if (Dy != 0.f) tmy *= ry;
+        if (Dz != 0.f) tmz *= rz;
+        const float tdx = fabsf(rx), tdy = fabsf(ry), tdz = fabsf(rz);
+        const int guard = (int)(fabsf(Dx) + fabsf(Dy) + fabsf(Dz)) + 4;
+        float t = 0.f;
+        int nstep = 0;
+        for (;;) {
+            const float tn = fminf(tmx, fminf(tmy, tmz));
+            if (!(tn < 1.f)) {
+                run = fmaf(1.f - t, len, run);
+                break;
+            }
+            const float tc = fmaxf(tn, t);
+            run = fmaf(tc - t, len, run);
+            if (run > 0.f) on_run(ix, iy, iz, run);
+            run = 0.f;
+            if (tmx == tn) { ix += sx; tmx += tdx; }
+            if (tmy == tn) { iy += sy; tmy += tdy; }
+            if (tmz == tn) { iz += sz; tmz += tdz; }
+            t = tc;
+            if (++nstep > guard) {
+                atomicOr(flags, kFlagWalkGuard);
+                break;
+            }
+        }
+        ax = bx;
+        ay = by;
+        az = bz;
+    }
+    if (run > 0.f) on_run(ix, iy, iz, run);
+}
+
+// Pass-1 run sink: the hull byte (and x) of a run are loaded when the run is
+// emitted and used when the next run is emitted, so the loads overlap the
+// arithmetic of the walk.
+// Grid extent a sink needs (passed by value: taking the address of a kernel
+// parameter would force a stack copy).
+struct Dims {
+    int nx, ny, nz;
+    __device__ __forceinline__ bool inside(int ix, int iy, int iz) const
+    {
+        return (unsigned)ix < (unsigned)nx && (unsigned)iy < (unsigned)ny && (unsigned)iz < (unsigned)nz;
+    }
+    __device__ __forceinline__ int index(int ix, int iy, int iz) const { return ix + nx * (iy + ny * iz); }
+};
+
+template <int RL, bool DOT>
+struct StoreSink {
+    Dims g;
+    const uint8_t* __restrict__ mask;
+    const float* __restrict__ x;
+    RunSlots slots;
+    int lane;
+    LaneWalk* w;
+    int pj;
+    float pl, px;
+    uint8_t pm;
+    bool pending;
+
+    __device__ __forceinline__ void commit()
+    {
+        if (!pending) return;
+        if (!w->any) {
+            w->any = true;
+            w->head_j = pj;
+            w->head_l = pl;
+            w->head_in = pm != 0;
+        }
+        w->tail_j = pj;
+        w->tail_l = pl;
+        w->tail_in = pm != 0;
+        if (pm) {
+            if (DOT) w->s = fmaf(pl, px, w->s);
+            w->q = fmaf(pl, pl, w->q);
+            if (w->n < RL) {
+                slots.j[w->n * kWarp + lane] = pj;
+                slots.l[w->n * kWarp + lane] = pl;
+            }
+            ++w->n;
+        }
+    }
+    __device__ __forceinline__ void operator()(int ix, int iy, int iz, float l)
+    {
+        int j = -1;
+        uint8_t m = 0;
+        float xv = 0.f;
+        if (g.inside(ix, iy, iz)) {
+            j = g.index(ix, iy, iz);
+            m = __ldg(mask + j);
+            if (DOT) xv = __ldg(x + j);
+        }
+        commit();
+        pj = j;
+        pl = l;
+        px = xv;
+        pm = m;
+        pending = true;
+    }
+};
+
+// Lane range of a proton with nseg segments.
+__device__ __forceinline__ void lane_range(const Path& P, int cmin, int lane, int& k0, int& k1)
+{
+    int C = (P.nseg + kWarp - 1) / kWarp;
+    if (C < cmin) C = cmin;
+    k0 = lane * C;
+    k1 = min(k0 + C, P.nseg);
+}
+
+// Pass 1 for the proton P on the calling warp: walk, store, accumulate, and
+// resolve the runs shared by neighbouring lanes.  Returns the warp-reduced
+// (s, q) on every lane.
+template <int RL, bool DOT>
+__device__ __forceinline__ void warp_walk(const Path& P, const MlpC& mc, const GridC& g,
+                                          const uint8_t* __restrict__ mask,
+                                          const float* __restrict__ x, unsigned* flags,
+                                          RunSlots slots, int cmin, LaneWalk& w, float& s_all,
+                                          float& q_all)
+{
+    const int lane = threadIdx.x & (kWarp - 1);
+    lane_range(P, cmin, lane, w.k0, w.k1);
+    w.n = 0;
+    w.any = false;
+    w.head_j = w.tail_j = -1;
+    w.head_l = w.tail_l = 0.f;
+    w.head_in = w.tail_in = false;
+    w.s = w.q = 0.f;
+    w.ends = range_ends(P, mc, g, w.k0, w.k1);
+    if (w.k0 < w.k1) {
+        StoreSink<RL, DOT> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, lane, &w, -1, 0.f, 0.f, 0, false};
+        walk_points(P, mc, g, flags, w.k0, w.k1, w.ends, sink);
+        sink.commit();
+    }
+    const unsigned full = 0xffffffffu;
+    const int pt_j = __shfl_up_sync(full, w.tail_j, 1);
+    const float pt_l = __shfl_up_sync(full, w.tail_l, 1);
+    const bool p_any = __shfl_up_sync(full, (int)w.any, 1) != 0;
+    w.merged_prev = lane > 0 && p_any && w.any && w.head_j >= 0 && pt_j == w.head_j;
+    w.next_merges = __shfl_down_sync(full, (int)w.merged_prev, 1) != 0 && lane < kWarp - 1;
+    w.next_head_l = __shfl_down_sync(full, w.head_l, 1);
+    float q = w.q;
+    if (w.merged_prev && w.head_in) q = fmaf(2.f * pt_l, w.head_l, q);
+    float s = w.s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(full, s, o);
+        q += __shfl_xor_sync(full, q, o);
+    }
+    s_all = s;
+    q_all = q;
+}
+
+// Scatter sink used when a lane re-walks its range (more runs than slots):
+// drops the head run owned by the previous lane and extends the tail run by the
+// next lane's head piece.
+template <class Op>
+struct RewalkSink {
+    Dims g;
+    const uint8_t* __restrict__ mask;
+    const LaneWalk* w;
+    Op op;
+    int pj;
+    float pl;
+    uint8_t pm;
+    bool pending, first;
+    __device__ __forceinline__ void flush(bool last)
+    {
+        if (!pending || !pm) return;
+        if (first && w->merged_prev) return;
+        float l = pl;
+        if (last && w->next_merges) l += w->next_head_l;
+        op(pj, l);
+    }
+    __device__ __forceinline__ void operator()(int ix, int iy, int iz, float l)
+    {
+        int j = -1;
+        uint8_t m = 0;
+        if (g.inside(ix, iy, iz)) {
+            j = g.index(ix, iy, iz);
+            m = __ldg(mask + j);
+        }
+        if (pending) {
+            flush(false);
+            first = false;
+        }
+        pj = j;
+        pl = l;
+        pm = m;
+        pending = true;
+    }
+};
+
+// Replay (or re-walk) this lane's hull runs with their final ownership:
+// op(j, chord) once per run of the row.
+template <int RL, class Op>
+__device__ __forceinline__ void replay_runs(const Path& P, const MlpC& mc, const GridC& g,
+                                            const uint8_t* __restrict__ mask, unsigned* flags,
+                                            RunSlots slots, const LaneWalk& w, Op op)
+{
+    if (w.k0 >= w.k1) return;
+    const int lane = threadIdx.x & (kWarp - 1);
+    if (w.n <= RL) {
+        for (int e = 0; e < w.n; ++e) {
+            if (e == 0 && w.merged_prev && w.head_in) continue;
+            float l = slots.l[e * kWarp + lane];
+            if (e == w.n - 1 && w.next_merges && w.tail_in) l += w.next_head_l;
+            op(slots.j[e * kWarp + lane], l);
+        }
+    } else {
+        RewalkSink<Op> sink{Dims{g.nx, g.ny, g.nz}, mask, &w, op, -1, 0.f, 0, false, true};
+        walk_points(P, mc, g, flags, w.k0, w.k1, w.ends, sink);
+        sink.flush(true);
+    }
+}
+
+}  // namespace pct

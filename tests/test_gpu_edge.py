@@ -142,7 +142,7 @@ def test_anisotropic_voxels_offset_origin_and_fine_mlp_step(cuda_device):
     hull = ((x * x + y * y) <= 27.0 ** 2).astype(np.uint8).reshape(-1)
     for du_um in (None, 500):
         geo = O.Geometry(shape, voxel, origin, mask=hull, du=None if du_um is None else du_um / 1000)
-        rowptr, j, ln, margin = O.rows(geo, h)
+        rowptr, j, ln, margin, cond = O.rows(geo, h, with_cond=True)
         ctx = pct.Context(shape, voxel, origin, hull=hull)
         if du_um is not None:
             ctx.set_option(pct.PCT_OPT_MLP_STEP_UM, du_um)
@@ -150,7 +150,8 @@ def test_anisotropic_voxels_offset_origin_and_fine_mlp_step(cuda_device):
         gidx, glen, gnnz = ctx.rows(max_nnz=256)
         rows, excused, worst, bad = U.compare_rows(gidx.cpu().numpy(),
                                                    glen.cpu().numpy().astype(np.float64),
-                                                   gnnz.cpu().numpy(), rowptr, j, ln, margin)
+                                                   gnnz.cpu().numpy(), rowptr, j, ln, margin,
+                                                   cond=cond)
         assert not bad, bad[:5]
         assert excused <= 0.02 * rows
         ctx.close()

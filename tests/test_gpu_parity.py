@@ -21,10 +21,10 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def tiny(cuda_device):
     cfg, rsp, hull, hist = U.scan("tiny")
-    geo, rowptr, j, ln, margin, A = U.oracle_rows("tiny")
+    geo, rowptr, j, ln, margin, A, cond = U.oracle_rows("tiny")
     ctx = U.context(cfg, hull, hist)
     yield dict(cfg=cfg, rsp=rsp, hull=hull, hist=hist, geo=geo, rowptr=rowptr, j=j, ln=ln,
-               margin=margin, A=A, ctx=ctx)
+               margin=margin, A=A, cond=cond, ctx=ctx)
     ctx.close()
 
 
@@ -74,8 +74,12 @@ def test_rows_match_oracle_bit_exact_except_near_face(tiny):
     n = ctx.n
     gidx, glen, gnnz = ctx.rows(0, n, max_nnz=256)
     assert int(gnnz.max()) <= 256
+    st = ctx.hull_states().cpu().numpy().astype(np.float64)
+    ost, _, _ = O.prepare(tiny["geo"], tiny["hist"])
+    dL = np.abs((st[:, 1] - st[:, 0]) - (ost[:, 1] - ost[:, 0]))
     res = U.compare_rows(gidx.cpu().numpy(), glen.cpu().numpy().astype(np.float64),
-                         gnnz.cpu().numpy(), tiny["rowptr"], tiny["j"], tiny["ln"], tiny["margin"])
+                         gnnz.cpu().numpy(), tiny["rowptr"], tiny["j"], tiny["ln"], tiny["margin"],
+                         cond=tiny["cond"], dL=dL)
     rows, excused, worst, bad = res
     print("rows %d, near-face excused %d, worst chord diff %.3g mm" % (rows, excused, worst))
     assert not bad, bad[:10]

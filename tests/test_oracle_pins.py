@@ -427,3 +427,25 @@ def test_tv_closed_forms():
     step[:, :, 3:] = 1.0
     v, _ = O.tv(step.reshape(-1), shape, eps=1e-9)
     assert abs(v - 4 * 5 * 1.0) < 1e-6
+
+
+def test_csr_leaves_path_order_rows_untouched():
+    # building A must not reorder the caller's path-order rows
+    rowptr = np.array([0, 3], dtype=np.int64)
+    j = np.array([5, 1, 3], dtype=np.int32)
+    ln = np.array([0.5, 0.25, 0.75])
+    A = O.csr(rowptr, j, ln, 8)
+    assert j.tolist() == [5, 1, 3] and ln.tolist() == [0.5, 0.25, 0.75]
+    assert A.indices.tolist() == [1, 3, 5] and A.data.tolist() == [0.25, 0.75, 0.5]
+
+
+def test_walk_consecutive_segments_share_their_vertex():
+    # samples every 0.8 mm along x on a 1.6 mm grid put every other vertex on a
+    # face (up to rounding); the walk must still move monotonically in x
+    geo = _geo(shape=(40, 4, 4), voxel=(1.6, 1.25, 0.8), origin=(-33.0, -2.5, -1.6))
+    xs = -26.6 + 0.8 * np.arange(67)
+    pts = np.stack([xs, np.full_like(xs, 0.3), np.full_like(xs, 0.1)], axis=1)
+    j, ln, _ = O.walk(geo, pts)
+    ix = j % 40
+    assert np.all(np.diff(ix) == 1), ix
+    assert np.all(ln[1:-1] > 1.5)
