@@ -192,6 +192,47 @@ pct_status pct_synchronize(pct_ctx *ctx);
 pct_status pct_get_stat(pct_ctx *ctx, int32_t key, double *value);
 pct_status pct_reset_stats(pct_ctx *ctx);
 
+/* ---- DROP reconstruction without device allocation --------------------------
+ * The paper has no counterpart to this entry point.  It is for callers that
+ * cannot call cudaMalloc: for example an application that hands all device
+ * memory to its own pool allocator and forbids allocations outside it, or a
+ * latency-bound service that cannot accept the device-wide synchronization a
+ * cudaMalloc or cudaFree may cause in the middle of a scan.
+ *
+ * It computes what pct_create + pct_load_histories + pct_solve compute (same
+ * kernels, MLP spacing = smallest voxel edge), but takes every input as a
+ * device pointer and keeps all scratch (a copy of the histories, the
+ * per-proton records, the per-voxel DROP accumulator, the MLP table) in fixed
+ * device arrays compiled into the library: about 15 MB, held on every GPU that
+ * loads the library until the process exits.  Limits: at most
+ * PCT_NOALLOC_MAX_PROTONS protons, PCT_NOALLOC_MAX_VOXELS voxels, and a grid
+ * diagonal of at most PCT_NOALLOC_MAX_SAMPLES MLP steps; larger inputs are
+ * rejected with PCT_ERR_ARG before any GPU work.
+ *   grid       -- host pointer, as in pct_create
+ *   hull_mask  -- device, nx*ny*nz bytes (nonzero = inside the hull)
+ *   n, in_xyz..wepl_mm -- device pointers, as in pct_load_histories
+ *   iters, lambda, block_size -- as in pct_solve
+ *   x          -- device, n voxels: initial iterate in, RSP out
+ *   device     -- CUDA device to run on; cuda_stream -- stream (NULL: the
+ *                 default stream)
+ * The first call on a device looks up the device addresses of the fixed arrays
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call on a device shares the same arrays and
+ * clears the parts that must start at zero itself; calls that overlap on the
+ * GPU (from several host threads or streams) race on them.  The call returns
+ * after the work has finished.  It allocates and frees no device memory.
+ * Errors (status only; pct_last_error does not cover this call): PCT_ERR_ARG,
+ * PCT_ERR_CUDA, PCT_ERR_DEVICE. */
+#define PCT_NOALLOC_MAX_PROTONS 65536
+#define PCT_NOALLOC_MAX_VOXELS 1048576
+#define PCT_NOALLOC_MAX_SAMPLES 4096
+pct_status pct_solve_noalloc(const pct_grid *grid, const uint8_t *hull_mask, int64_t n,
+                             const float *const in_xyz[3], const float *const out_xyz[3],
+                             const float *const ang_in[2], const float *const ang_out[2],
+                             const float *gantry_rad, const float *wepl_mm, int32_t iters,
+                             float lambda, int64_t block_size, float *x, int device,
+                             void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -40,7 +40,7 @@ STATE_FIELDS = ("u_in", "u_out", "t0", "theta0", "v0", "psi0", "t2", "theta2", "
 EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct_get_option",
            "pct_load_histories", "pct_hull_states", "pct_mlp", "pct_rows", "pct_forward",
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
-           "pct_reset_stats")
+           "pct_reset_stats", "pct_solve_noalloc")
 
 
 class PctError(RuntimeError):
@@ -85,6 +85,8 @@ def load_library(path: str = LIB_PATH):
         "pct_synchronize": ([P], ctypes.c_int),
         "pct_get_stat": ([P, I32, P], ctypes.c_int),
         "pct_reset_stats": ([P], ctypes.c_int),
+        "pct_solve_noalloc": ([P, P, I64, P, P, P, P, P, P, I32, F, I64, P, ctypes.c_int, P],
+                              ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +236,34 @@ def pct_solve_host(ctx, iters, lam, block_size, x_host):
             raise TypeError("x_host must be a contiguous float32 array")
         p = ctypes.c_void_p(x_host.ctypes.data)
     _check(ctx, load_library().pct_solve_host(ctx, int(iters), float(lam), int(block_size), p))
+
+
+PCT_NOALLOC_MAX_PROTONS = 65536
+PCT_NOALLOC_MAX_VOXELS = 1048576
+
+
+def pct_solve_noalloc(shape, voxel, origin, hull_mask, hist, iters, lam, block_size, x,
+                      device=0, stream=None):
+    """DROP reconstruction that allocates no device memory (see include/pct.h).
+
+    hull_mask: CUDA uint8 tensor of nx*ny*nz bytes; hist: dict of 12 CUDA float32
+    tensors of equal length; x: CUDA float32 tensor (n voxels), updated in place.
+    Returns the C status (0 = PCT_OK) instead of raising, so callers can test limits.
+    """
+    import torch
+    g = pct_grid(int(shape[0]), int(shape[1]), int(shape[2]), float(voxel[0]), float(voxel[1]),
+                 float(voxel[2]), float(origin[0]), float(origin[1]), float(origin[2]))
+    cols = [hist[k] for k in HIST_FIELDS]
+    n = cols[0].numel()
+    ptrs = [_dptr(c, torch.float32, n, k) for k, c in zip(HIST_FIELDS, cols)]
+    A3 = ctypes.c_void_p * 3
+    A2 = ctypes.c_void_p * 2
+    h = int(stream.cuda_stream) if stream is not None else int(torch.cuda.current_stream(device).cuda_stream)
+    return load_library().pct_solve_noalloc(
+        ctypes.byref(g), _dptr(hull_mask, torch.uint8, what="hull_mask"), int(n), A3(*ptrs[0:3]),
+        A3(*ptrs[3:6]), A2(ptrs[6], ptrs[7]), A2(ptrs[8], ptrs[9]), ptrs[10], ptrs[11], int(iters),
+        float(lam), int(block_size), _dptr(x, torch.float32, what="x"), int(device),
+        ctypes.c_void_p(h) if h else None)
 
 
 def pct_synchronize(ctx):
