@@ -45,6 +45,8 @@ def _args():
     p.add_argument("--protons", type=int, default=None, help="override the proton count")
     p.add_argument("--block", type=int, default=None)
     p.add_argument("--cta", type=int, default=None)
+    p.add_argument("--mode", default="fused", choices=["fused", "csr", "packed"],
+                   help="row form: recomputed on the fly, or stored (built once, timed apart)")
     p.add_argument("--cpu-sample", type=int, default=320000)
     p.add_argument("--ref-sample", type=int, default=100000)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -261,7 +263,16 @@ def run_ours(args):
     ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=local)
     if args.cta:
         ctx.set_option(pct.PCT_OPT_CTA_THREADS, args.cta)
+    mode = {"fused": pct.PCT_MODE_FUSED, "csr": pct.PCT_MODE_CSR, "packed": pct.PCT_MODE_PACKED}[args.mode]
+    ctx.set_option(pct.PCT_OPT_MODE, mode)
     ctx.load_histories(hist)
+    build_s = None
+    if mode != pct.PCT_MODE_FUSED:
+        torch.cuda.synchronize(dev)
+        tb = time.perf_counter()
+        ctx.build_rows()
+        ctx.synchronize()
+        build_s = time.perf_counter() - tb
 
     # rows crossing the hull, and the mean path size of a sample (work model)
     valid = 0
@@ -328,7 +339,7 @@ def run_ours(args):
     flops_launch = fused_flops(valid, mean_pts, mean_nnz) / blocks_per_iter
     achieved = flops_launch / avg_launch_s / 1e12
     hbm_bytes_launch = (n / blocks_per_iter) * (16 * 4)        # proton records streamed per launch
-    per_row_traffic = _profiled_traffic(cfg.name)
+    per_row_traffic = _profiled_traffic(cfg.name) if args.mode == "fused" else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": (per_row_traffic * valid / blocks_per_iter) if per_row_traffic else None,
@@ -342,11 +353,29 @@ def run_ours(args):
                 "hbm_gbs_algorithmic": hbm_bytes_launch / avg_launch_s / 1e9,
                 "hbm_peak_gbs": peaks.get("hbm_gbs"),
                 "fused_share_of_step": (fused_ms / args.steps) / step_ms if step_ms else None}
+    if args.mode != "fused":
+        # stored rows stream from HBM: entry bytes (8 CSR, 3 packed) + row offset + WEPL per row
+        entries = ctx.stat(pct.PCT_STAT_ROW_ENTRIES)
+        per_entry = 8.0 if args.mode == "csr" else 3.0
+        per_row = 8.0 + 4.0 + (8.0 if args.mode == "packed" else 0.0)
+        bytes_launch = (entries * per_entry + n * per_row) / blocks_per_iter
+        hbm_peak = float(peaks.get("hbm_gbs", 6400.0))
+        ach = bytes_launch / avg_launch_s / 1e9
+        roofline = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": None,
+                    "kernel": "k_drop_csr" if args.mode == "csr" else "k_drop_packed",
+                    "avg_launch_ms": avg_launch_s * 1e3, "launches_timed": fused_n,
+                    "bytes_model": "%.0f B/entry x %.4g entries + %.0f B/row, per iteration" % (
+                        per_entry, entries, per_row),
+                    "peak_source": "MEASURED_PEAKS hbm_gbs (copy bandwidth)",
+                    "fused_share_of_step": (fused_ms / args.steps) / step_ms if step_ms else None}
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": _config(cfg, block, n), "recon_s": step_ms * 1e-3,
+           "config": dict(_config(cfg, block, n), mode=args.mode), "recon_s": step_ms * 1e-3,
+           "row_build_s": build_s, "row_bytes": ctx.stat(pct.PCT_STAT_ROW_BYTES),
+           "row_entries": ctx.stat(pct.PCT_STAT_ROW_ENTRIES),
            "rows_in_hull": valid, "mean_nnz_per_row": mean_nnz, "mean_mlp_points": mean_pts,
            "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
 
@@ -383,6 +412,7 @@ def run_ours(args):
         sub_np = synth.to_numpy(sub)
         xo, dt, vs, threads = oracle_solve_timed(cfg, hull_np, sub_np, cfg.iters, cfg.lam, block)
         with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=local) as c2:
+            c2.set_option(pct.PCT_OPT_MODE, mode)
             c2.load_histories(sub)
             xg = torch.from_numpy(hull_np.astype(np.float32)).to(dev)
             c2.solve(xg, cfg.iters, cfg.lam, block)

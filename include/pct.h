@@ -72,9 +72,24 @@ enum pct_option {
     /* Device-memory cap in bytes for the context's own allocations; 0 = none.
      * An allocation that would pass it fails with PCT_ERR_OOM. */
     PCT_OPT_MEM_CAP_BYTES = 3,
-    /* 1: record CUDA events around each launch of the fused DROP kernel so that
+    /* 1: record CUDA events around each launch of the DROP block kernel so that
      * pct_get_stat(PCT_STAT_FUSED_MS) reports its device time.  Default 0. */
-    PCT_OPT_TIMING = 4
+    PCT_OPT_TIMING = 4,
+    /* How pct_solve gets the rows of A (one of enum pct_mode).  Default
+     * PCT_MODE_FUSED.  Changing it drops stored rows. */
+    PCT_OPT_MODE = 5
+};
+
+/* Row forms of pct_solve.  The stored forms are built by the same walk as the
+ * fused form (so they hold the same rows), once per loaded history set, by
+ * pct_build_rows or by the first pct_solve that needs them; they are dropped by
+ * pct_load_histories and by a change of mode or MLP step. */
+enum pct_mode {
+    PCT_MODE_FUSED = 0,  /* recompute MLP and walk for every row of every block: no storage */
+    PCT_MODE_CSR = 1,    /* int64 row offsets + int32 voxel + FP32 chord per entry (8 B) */
+    PCT_MODE_PACKED = 2  /* int64 row offsets + first voxel per row + per entry a 1-byte 3D step
+                            code with an in-hull bit and an FP16 chord (3 B); runs outside the
+                            hull are kept (weight 0) so that steps stay between neighbours */
 };
 
 /* Keys of pct_get_stat.  Counters cover the calls since pct_reset_stats. */
@@ -85,7 +100,9 @@ enum pct_stat {
                                      synchronizes the stream) */
     PCT_STAT_DEVICE_BYTES = 4,    /* device memory held by the context */
     PCT_STAT_N_PROTONS = 5,       /* protons loaded */
-    PCT_STAT_N_HULL_VOXELS = 6    /* voxels inside the hull mask */
+    PCT_STAT_N_HULL_VOXELS = 6,   /* voxels inside the hull mask */
+    PCT_STAT_ROW_ENTRIES = 7,     /* entries of the stored rows (0 when none) */
+    PCT_STAT_ROW_BYTES = 8        /* device bytes of the stored rows */
 };
 
 /* Create a context on CUDA device `device`.
@@ -179,6 +196,12 @@ pct_status pct_adjoint(pct_ctx *ctx, const float *y, float *g);
  * Errors: PCT_ERR_ARG (null x, iters < 0, block_size < 1), PCT_ERR_STATE,
  * PCT_ERR_OOM, PCT_ERR_CUDA. */
 pct_status pct_solve(pct_ctx *ctx, int32_t iters, float lambda, int64_t block_size, float *x);
+
+/* Build the stored rows of the current mode (PCT_OPT_MODE) for the loaded
+ * histories (Sec. I, the path data of A).  No-op in PCT_MODE_FUSED.  Enqueued
+ * on the context stream; synchronizes once to size the entry arrays.
+ * Errors: PCT_ERR_STATE (no histories), PCT_ERR_OOM, PCT_ERR_CUDA. */
+pct_status pct_build_rows(pct_ctx *ctx);
 
 /* As pct_solve, with x in host memory: copies x to the device, solves, copies
  * the result back and synchronizes. */

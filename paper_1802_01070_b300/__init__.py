@@ -27,9 +27,10 @@ LIB_PATH = os.path.join(_PKG, "libpct.so")
 PCT_OK, PCT_ERR_ARG, PCT_ERR_CUDA, PCT_ERR_OOM, PCT_ERR_STATE, PCT_ERR_TIMEOUT, PCT_ERR_DEVICE = range(7)
 STATUS_NAMES = {0: "PCT_OK", 1: "PCT_ERR_ARG", 2: "PCT_ERR_CUDA", 3: "PCT_ERR_OOM",
                 4: "PCT_ERR_STATE", 5: "PCT_ERR_TIMEOUT", 6: "PCT_ERR_DEVICE"}
-PCT_OPT_CTA_THREADS, PCT_OPT_MLP_STEP_UM, PCT_OPT_MEM_CAP_BYTES, PCT_OPT_TIMING = 1, 2, 3, 4
+PCT_OPT_CTA_THREADS, PCT_OPT_MLP_STEP_UM, PCT_OPT_MEM_CAP_BYTES, PCT_OPT_TIMING, PCT_OPT_MODE = 1, 2, 3, 4, 5
+PCT_MODE_FUSED, PCT_MODE_CSR, PCT_MODE_PACKED = 0, 1, 2
 (PCT_STAT_LAUNCHES, PCT_STAT_FUSED_LAUNCHES, PCT_STAT_FUSED_MS, PCT_STAT_DEVICE_BYTES,
- PCT_STAT_N_PROTONS, PCT_STAT_N_HULL_VOXELS) = 1, 2, 3, 4, 5, 6
+ PCT_STAT_N_PROTONS, PCT_STAT_N_HULL_VOXELS, PCT_STAT_ROW_ENTRIES, PCT_STAT_ROW_BYTES) = 1, 2, 3, 4, 5, 6, 7, 8
 
 HIST_FIELDS = ("in_x", "in_y", "in_z", "out_x", "out_y", "out_z",
                "theta_in", "psi_in", "theta_out", "psi_out", "phi", "wepl")
@@ -40,7 +41,7 @@ STATE_FIELDS = ("u_in", "u_out", "t0", "theta0", "v0", "psi0", "t2", "theta2", "
 EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct_get_option",
            "pct_load_histories", "pct_hull_states", "pct_mlp", "pct_rows", "pct_forward",
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
-           "pct_reset_stats", "pct_solve_noalloc")
+           "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows")
 
 
 class PctError(RuntimeError):
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
         "pct_synchronize": ([P], ctypes.c_int),
         "pct_get_stat": ([P, I32, P], ctypes.c_int),
         "pct_reset_stats": ([P], ctypes.c_int),
+        "pct_build_rows": ([P], ctypes.c_int),
         "pct_solve_noalloc": ([P, P, I64, P, P, P, P, P, P, I32, F, I64, P, ctypes.c_int, P],
                               ctypes.c_int),
     }
@@ -266,6 +268,10 @@ def pct_solve_noalloc(shape, voxel, origin, hull_mask, hist, iters, lam, block_s
         ctypes.c_void_p(h) if h else None)
 
 
+def pct_build_rows(ctx):
+    _check(ctx, load_library().pct_build_rows(ctx))
+
+
 def pct_synchronize(ctx):
     _check(ctx, load_library().pct_synchronize(ctx))
 
@@ -430,6 +436,10 @@ class Context:
         with _Ordered(self):
             pct_solve_host(self._h, iters, lam, block_size, x_host)
         return x_host
+
+    def build_rows(self):
+        with _Ordered(self):
+            pct_build_rows(self._h)
 
     def synchronize(self):
         pct_synchronize(self._h)

@@ -43,6 +43,16 @@ struct pct_ctx {
     float* d_rec = nullptr;
     float2* d_acc = nullptr;
     float* d_xtmp = nullptr;
+    // stored rows (PCT_MODE_CSR / PCT_MODE_PACKED)
+    int mode = PCT_MODE_FUSED;
+    int rows_mode = -1;                  // mode the stored rows were built for (-1: none)
+    int64_t nnz = 0;
+    int64_t* d_rowptr = nullptr;
+    int32_t* d_idx = nullptr;
+    float* d_len = nullptr;
+    uint8_t* d_codes = nullptr;
+    void* d_lens16 = nullptr;
+    short4* d_start = nullptr;
     int cta = 256;
     int timing = 0;
     int64_t mem_cap = 0;
@@ -211,6 +221,117 @@ pct_status ensure_acc(pct_ctx* c)
     return PCT_OK;
 }
 
+int64_t row_bytes(const pct_ctx* c)
+{
+    int64_t b = 0;
+    for (void* p : {(void*)c->d_rowptr, (void*)c->d_idx, (void*)c->d_len, (void*)c->d_codes,
+                    c->d_lens16, (void*)c->d_start}) {
+        auto it = c->sizes.find(p);
+        if (p && it != c->sizes.end()) b += (int64_t)it->second;
+    }
+    return b;
+}
+
+void drop_rows(pct_ctx* c)
+{
+    if (c->rows_mode >= 0 && c->stream) cudaStreamSynchronize(c->stream);
+    dfree(c, c->d_rowptr);
+    dfree(c, c->d_idx);
+    dfree(c, c->d_len);
+    dfree(c, c->d_codes);
+    dfree(c, c->d_lens16);
+    dfree(c, c->d_start);
+    c->d_rowptr = nullptr;
+    c->d_idx = nullptr;
+    c->d_len = nullptr;
+    c->d_codes = nullptr;
+    c->d_lens16 = nullptr;
+    c->d_start = nullptr;
+    c->nnz = 0;
+    c->rows_mode = -1;
+}
+
+// Build the stored rows of the current mode: count entries per row, scan to
+// row offsets, allocate, fill.  Synchronizes once (to size the entry arrays).
+pct_status build_rows(pct_ctx* c)
+{
+    drop_rows(c);
+    if (c->mode == PCT_MODE_FUSED) return PCT_OK;
+    const int64_t m = c->n;
+    const Launch L = launch_of(c);
+    const Geo G = geo_of(c);
+    pct_status s = prepare(c);
+    if (s != PCT_OK) return s;
+    void *p_cnt = nullptr, *p_chunk = nullptr, *p = nullptr;
+    if ((s = dalloc(c, &p_cnt, (size_t)(m > 0 ? m : 1) * sizeof(int32_t), "row counts")) != PCT_OK) return s;
+    if ((s = dalloc(c, &p_chunk, (size_t)(scan_chunks(m) + 1) * sizeof(int64_t), "scan chunks")) != PCT_OK) {
+        dfree(c, p_cnt);
+        return s;
+    }
+    auto cleanup = [&]() {
+        dfree(c, p_cnt);
+        dfree(c, p_chunk);
+    };
+    if ((s = dalloc(c, &p, (size_t)(m + 1) * sizeof(int64_t), "row offsets")) != PCT_OK) {
+        cleanup();
+        return s;
+    }
+    c->d_rowptr = (int64_t*)p;
+    cudaError_t e;
+    if (c->mode == PCT_MODE_PACKED) {
+        if ((s = dalloc(c, &p, (size_t)(m > 0 ? m : 1) * sizeof(short4), "row starts")) != PCT_OK) {
+            cleanup();
+            drop_rows(c);
+            return s;
+        }
+        c->d_start = (short4*)p;
+        e = launch_pack_count(L, G, c->d_rec, c->stride, m, (int32_t*)p_cnt, c->d_start);
+    } else {
+        e = launch_csr_count(L, G, c->d_rec, c->stride, m, (int32_t*)p_cnt);
+    }
+    if (e == cudaSuccess) e = launch_row_scan(L, (const int32_t*)p_cnt, m, c->d_rowptr, (int64_t*)p_chunk);
+    int64_t nnz = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&nnz, c->d_rowptr + m, sizeof nnz, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess) {
+        drop_rows(c);
+        return cuda_fail(c, e, "row count");
+    }
+    // a row holds at most a few entries per voxel of the grid diagonal
+    if (nnz < 0 || nnz > m * (int64_t)(4 * (c->kmax + 8))) {
+        drop_rows(c);
+        return fail(c, PCT_ERR_DEVICE, "row count out of range (" + std::to_string(nnz) + " entries)");
+    }
+    const size_t ne = (size_t)(nnz > 0 ? nnz : 1);
+    if (c->mode == PCT_MODE_PACKED) {
+        if ((s = dalloc(c, &p, ne, "packed row codes")) == PCT_OK) {
+            c->d_codes = (uint8_t*)p;
+            if ((s = dalloc(c, &p, ne * 2, "packed row chords")) == PCT_OK) c->d_lens16 = p;
+        }
+        if (s == PCT_OK)
+            e = launch_pack_fill(L, G, c->d_rec, c->stride, m, c->d_rowptr, c->d_codes, c->d_lens16);
+    } else {
+        if ((s = dalloc(c, &p, ne * sizeof(int32_t), "CSR indices")) == PCT_OK) {
+            c->d_idx = (int32_t*)p;
+            if ((s = dalloc(c, &p, ne * sizeof(float), "CSR chords")) == PCT_OK) c->d_len = (float*)p;
+        }
+        if (s == PCT_OK) e = launch_csr_fill(L, G, c->d_rec, c->stride, m, c->d_rowptr, c->d_idx, c->d_len);
+    }
+    if (s != PCT_OK) {
+        drop_rows(c);
+        return s;
+    }
+    if (e != cudaSuccess) {
+        drop_rows(c);
+        return cuda_fail(c, e, "row fill");
+    }
+    c->nnz = nnz;
+    c->rows_mode = c->mode;
+    return PCT_OK;
+}
+
 cudaEvent_t next_event(pct_ctx* c)
 {
     if (c->ev_used == c->ev.size()) {
@@ -338,6 +459,7 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
         return PCT_OK;
     case PCT_OPT_MLP_STEP_UM: {
         if (value < 0 || value > 100000) return fail(c, PCT_ERR_ARG, "MLP step out of range");
+        drop_rows(c);
         const int64_t old = c->du_um;
         c->du_um = value;
         pct_status s = build_sigma_table(c);
@@ -350,6 +472,12 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
         return PCT_OK;
     case PCT_OPT_TIMING:
         c->timing = value ? 1 : 0;
+        return PCT_OK;
+    case PCT_OPT_MODE:
+        if (value != PCT_MODE_FUSED && value != PCT_MODE_CSR && value != PCT_MODE_PACKED)
+            return fail(c, PCT_ERR_ARG, "unknown mode");
+        if ((int)value != c->mode) drop_rows(c);
+        c->mode = (int)value;
         return PCT_OK;
     default:
         return fail(c, PCT_ERR_ARG, "unknown option key");
@@ -364,6 +492,7 @@ pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
     case PCT_OPT_MLP_STEP_UM: *value = (int64_t)std::llround(step_mm(c) * 1000.0); return PCT_OK;
     case PCT_OPT_MEM_CAP_BYTES: *value = c->mem_cap; return PCT_OK;
     case PCT_OPT_TIMING: *value = c->timing; return PCT_OK;
+    case PCT_OPT_MODE: *value = c->mode; return PCT_OK;
     default: return PCT_ERR_ARG;
     }
 }
@@ -376,6 +505,7 @@ pct_status pct_load_histories(pct_ctx* c, int64_t n, const float* const in_xyz[3
     if (!c) return PCT_ERR_ARG;
     if (n < 0) return fail(c, PCT_ERR_ARG, "negative proton count");
     DeviceGuard dg(c->device);
+    drop_rows(c);
     if (n == 0) {
         c->n = 0;
         c->loaded = true;
@@ -509,7 +639,11 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
     if (s != PCT_OK) return s;
     if (c->n == 0 || iters == 0) return PCT_OK;
     if ((s = ensure_acc(c)) != PCT_OK) return s;
-    if ((s = prepare(c)) != PCT_OK) return s;
+    if (c->mode == PCT_MODE_FUSED) {
+        if ((s = prepare(c)) != PCT_OK) return s;
+    } else if (c->rows_mode != c->mode) {
+        if ((s = build_rows(c)) != PCT_OK) return s;
+    }
     cudaError_t e = cudaMemsetAsync(c->d_acc, 0, (size_t)c->n_vox * sizeof(float2), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "accumulator clear");
     const Launch L = launch_of(c);
@@ -523,7 +657,14 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
                 e1 = next_event(c);
                 if (e0) cudaEventRecord(e0, c->stream);
             }
-            e = launch_drop_fused(L, G, c->d_rec, c->stride, first, count, x, c->d_acc);
+            const float* b = c->d_hist + (size_t)H_WEPL * c->stride;
+            if (c->mode == PCT_MODE_CSR)
+                e = launch_drop_csr(L, c->d_flags, c->d_rowptr, c->d_idx, c->d_len, b, first, count, x, c->d_acc);
+            else if (c->mode == PCT_MODE_PACKED)
+                e = launch_drop_packed(L, c->gc, c->d_flags, c->d_rowptr, c->d_start, c->d_codes, c->d_lens16, b,
+                                       first, count, x, c->d_acc);
+            else
+                e = launch_drop_fused(L, G, c->d_rec, c->stride, first, count, x, c->d_acc);
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP kernel");
             ++c->fused_launches;
             if (e1) cudaEventRecord(e1, c->stream);
@@ -532,6 +673,15 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
         }
     }
     return PCT_OK;
+}
+
+pct_status pct_build_rows(pct_ctx* c)
+{
+    if (!c) return PCT_ERR_ARG;
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s != PCT_OK) return s;
+    return build_rows(c);
 }
 
 pct_status pct_solve_host(pct_ctx* c, int32_t iters, float lambda, int64_t block_size, float* x_host)
@@ -572,6 +722,8 @@ pct_status pct_synchronize(pct_ctx* c)
         if (flags & kFlagHullGuard) m += " hull search step bound exceeded;";
         if (flags & kFlagMlpTable) m += " MLP sample beyond table;";
         if (flags & kFlagRowSlots) m += " a row too long for pct_rows (nnz reported as -1);";
+        if (flags & kFlagPackStep) m += " packed rows: non-neighbouring consecutive voxels;";
+        if (flags & kFlagRowBounds) m += " stored row length or voxel index out of range;";
         return fail(c, PCT_ERR_DEVICE, m);
     }
     return PCT_OK;
@@ -599,6 +751,8 @@ pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
     case PCT_STAT_DEVICE_BYTES: *value = (double)c->mem_used; return PCT_OK;
     case PCT_STAT_N_PROTONS: *value = (double)c->n; return PCT_OK;
     case PCT_STAT_N_HULL_VOXELS: *value = (double)c->n_hull; return PCT_OK;
+    case PCT_STAT_ROW_ENTRIES: *value = (double)c->nnz; return PCT_OK;
+    case PCT_STAT_ROW_BYTES: *value = (double)row_bytes(c); return PCT_OK;
     default: return fail(c, PCT_ERR_ARG, "unknown stat key");
     }
 }

@@ -32,6 +32,8 @@ constexpr unsigned kFlagWalkGuard = 1u;   // a segment walk exceeded its step bo
 constexpr unsigned kFlagHullGuard = 2u;   // a hull search exceeded its step bound
 constexpr unsigned kFlagMlpTable = 4u;    // MLP sample index beyond the S1 table
 constexpr unsigned kFlagRowSlots = 8u;    // a debug row had more runs per lane than its slots
+constexpr unsigned kFlagPackStep = 16u;   // packed rows: consecutive runs not in neighbouring voxels
+constexpr unsigned kFlagRowBounds = 32u;  // a stored row's length or voxel index out of range
 
 struct GridC {
     int nx, ny, nz;
