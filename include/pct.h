@@ -197,6 +197,27 @@ pct_status pct_adjoint(pct_ctx *ctx, const float *y, float *g);
  * PCT_ERR_OOM, PCT_ERR_CUDA. */
 pct_status pct_solve(pct_ctx *ctx, int32_t iters, float lambda, int64_t block_size, float *x);
 
+/* ---- Gradient-based reconstruction beside DROP -----------------------------
+ * The paper solves A x = b with DROP only (Sec. IV-B).  With pct_forward and
+ * pct_adjoint as a differentiable projector, a caller can instead minimise
+ * ||A x - b||^2 + w TV(x); the two calls below supply the rest.  Neither has a
+ * counterpart in the paper. */
+
+/* Isotropic total variation of the volume x (device, n voxels):
+ *   value = sum over all voxels v of sqrt(|D+ x|_v^2 + eps^2),
+ * D+ the forward differences along x, y, z (zero at each axis' last index).
+ * grad (device, n floats, overwritten) = d value / d x; value (device, one
+ * double, overwritten).  Enqueued on the context stream.
+ * Errors: PCT_ERR_ARG (null pointer, eps < 0), PCT_ERR_CUDA. */
+pct_status pct_tv(pct_ctx *ctx, const float *x, float eps, float *grad, double *value);
+
+/* One Adam step (Kingma & Ba) on n parameters, all device arrays:
+ *   m <- b1 m + (1-b1) g;  v <- b2 v + (1-b2) g^2;
+ *   x <- x - lr (m / (1 - b1^step)) / (sqrt(v / (1 - b2^step)) + eps).
+ * step counts from 1.  Errors: PCT_ERR_ARG, PCT_ERR_CUDA. */
+pct_status pct_adam(pct_ctx *ctx, float *x, const float *grad, float *m, float *v, int64_t n,
+                    float lr, float beta1, float beta2, float eps, int32_t step);
+
 /* Build the stored rows of the current mode (PCT_OPT_MODE) for the loaded
  * histories (Sec. I, the path data of A).  No-op in PCT_MODE_FUSED.  Enqueued
  * on the context stream; synchronizes once to size the entry arrays.

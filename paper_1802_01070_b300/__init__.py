@@ -41,7 +41,7 @@ STATE_FIELDS = ("u_in", "u_out", "t0", "theta0", "v0", "psi0", "t2", "theta2", "
 EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct_get_option",
            "pct_load_histories", "pct_hull_states", "pct_mlp", "pct_rows", "pct_forward",
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
-           "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows")
+           "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam")
 
 
 class PctError(RuntimeError):
@@ -87,6 +87,8 @@ def load_library(path: str = LIB_PATH):
         "pct_get_stat": ([P, I32, P], ctypes.c_int),
         "pct_reset_stats": ([P], ctypes.c_int),
         "pct_build_rows": ([P], ctypes.c_int),
+        "pct_tv": ([P, P, F, P, P], ctypes.c_int),
+        "pct_adam": ([P, P, P, P, P, I64, F, F, F, F, I32], ctypes.c_int),
         "pct_solve_noalloc": ([P, P, I64, P, P, P, P, P, P, I32, F, I64, P, ctypes.c_int, P],
                               ctypes.c_int),
     }
@@ -268,6 +270,23 @@ def pct_solve_noalloc(shape, voxel, origin, hull_mask, hist, iters, lam, block_s
         ctypes.c_void_p(h) if h else None)
 
 
+def pct_tv(ctx, x, eps, grad, value):
+    import torch
+    _check(ctx, load_library().pct_tv(ctx, _dptr(x, torch.float32, what="x"), float(eps),
+                                      _dptr(grad, torch.float32, what="grad"),
+                                      _dptr(value, torch.float64, 1, "value")))
+
+
+def pct_adam(ctx, x, grad, m, v, lr, beta1, beta2, eps, step):
+    import torch
+    n = x.numel()
+    _check(ctx, load_library().pct_adam(ctx, _dptr(x, torch.float32, what="x"),
+                                        _dptr(grad, torch.float32, n, "grad"),
+                                        _dptr(m, torch.float32, n, "m"), _dptr(v, torch.float32, n, "v"),
+                                        int(n), float(lr), float(beta1), float(beta2), float(eps),
+                                        int(step)))
+
+
 def pct_build_rows(ctx):
     _check(ctx, load_library().pct_build_rows(ctx))
 
@@ -436,6 +455,21 @@ class Context:
         with _Ordered(self):
             pct_solve_host(self._h, iters, lam, block_size, x_host)
         return x_host
+
+    def tv(self, x, eps=1e-6, grad=None):
+        """(value as a 0-d float64 tensor, gradient) of the isotropic TV of x."""
+        import torch
+        g = torch.empty(self.n_vox, dtype=torch.float32, device=self.device) if grad is None else grad
+        val = torch.empty(1, dtype=torch.float64, device=self.device)
+        _dptr(x, torch.float32, self.n_vox, "x")
+        _dptr(g, torch.float32, self.n_vox, "grad")
+        with _Ordered(self):
+            pct_tv(self._h, x, eps, g, val)
+        return val[0], g
+
+    def adam(self, x, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        with _Ordered(self):
+            pct_adam(self._h, x, grad, m, v, lr, beta1, beta2, eps, step)
 
     def build_rows(self):
         with _Ordered(self):

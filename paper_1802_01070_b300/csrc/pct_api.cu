@@ -675,6 +675,29 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
     return PCT_OK;
 }
 
+pct_status pct_tv(pct_ctx* c, const float* x, float eps, float* grad, double* value)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!x || !grad || !value) return fail(c, PCT_ERR_ARG, "null x, grad or value");
+    if (!(eps >= 0.f) || !std::isfinite(eps)) return fail(c, PCT_ERR_ARG, "eps must be finite and >= 0");
+    DeviceGuard dg(c->device);
+    cudaError_t e = launch_tv(launch_of(c), x, c->grid.nx, c->grid.ny, c->grid.nz, eps, grad, value);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "TV kernel");
+}
+
+pct_status pct_adam(pct_ctx* c, float* x, const float* grad, float* m, float* v, int64_t n, float lr,
+                    float beta1, float beta2, float eps, int32_t step)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (n < 0 || (n > 0 && (!x || !grad || !m || !v))) return fail(c, PCT_ERR_ARG, "null vector or n < 0");
+    if (step < 1 || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+        !std::isfinite(lr) || !(eps > 0.f))
+        return fail(c, PCT_ERR_ARG, "Adam: step >= 1, 0 <= beta < 1, eps > 0, finite lr");
+    DeviceGuard dg(c->device);
+    cudaError_t e = launch_adam(launch_of(c), x, grad, m, v, n, lr, beta1, beta2, eps, step);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "Adam kernel");
+}
+
 pct_status pct_build_rows(pct_ctx* c)
 {
     if (!c) return PCT_ERR_ARG;

@@ -45,6 +45,12 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
                               int64_t first, int64_t count, const float* x, float2* acc);
 cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda);
 
+// gradient-based reconstruction (pct_grad.cu)
+cudaError_t launch_tv(const Launch& L, const float* x, int nx, int ny, int nz, float eps, float* grad,
+                      double* value);
+cudaError_t launch_adam(const Launch& L, float* x, const float* g, float* m, float* v, int64_t n,
+                        float lr, float b1, float b2, float eps, int step);
+
 // stored rows (pct_rows.cu)
 int64_t scan_chunks(int64_t m);
 cudaError_t launch_csr_count(const Launch& L, const Geo& G, const float* rec, int64_t stride,
