@@ -77,7 +77,23 @@ enum pct_option {
     PCT_OPT_TIMING = 4,
     /* How pct_solve gets the rows of A (one of enum pct_mode).  Default
      * PCT_MODE_FUSED.  Changing it drops stored rows. */
-    PCT_OPT_MODE = 5
+    PCT_OPT_MODE = 5,
+    /* pct_solve_batch with this context first: 1 = capture the batch (record
+     * preparation, clears, persistent launch) in a CUDA graph on the first call
+     * and replay it while the batch arguments stay the same.  Default 0. */
+    PCT_OPT_GRAPH = 6,
+    /* pct_solve_batch with this context first: 1 = on the first call with a new
+     * batch, time one iteration with 128- and 256-thread CTAs (on scratch
+     * copies of x) and keep the faster.  Default 0 (use PCT_OPT_CTA_THREADS). */
+    PCT_OPT_AUTOTUNE = 7,
+    /* Polls a batched-solve barrier wait makes before giving up (each poll
+     * sleeps ~64 ns); a wait that gives up ends the launch and
+     * pct_synchronize returns PCT_ERR_TIMEOUT.  1..2^30, default 2^27. */
+    PCT_OPT_SPIN_LIMIT = 8,
+    /* Test only: 1 = the first barrier of the batch's first scan waits for one
+     * arrival more than its CTAs make, so the wait runs out (exercises the
+     * timeout path without any fault).  Default 0. */
+    PCT_OPT_TEST_UNREACHABLE_BARRIER = 9
 };
 
 /* Row forms of pct_solve.  The stored forms are built by the same walk as the
@@ -102,7 +118,10 @@ enum pct_stat {
     PCT_STAT_N_PROTONS = 5,       /* protons loaded */
     PCT_STAT_N_HULL_VOXELS = 6,   /* voxels inside the hull mask */
     PCT_STAT_ROW_ENTRIES = 7,     /* entries of the stored rows (0 when none) */
-    PCT_STAT_ROW_BYTES = 8        /* device bytes of the stored rows */
+    PCT_STAT_ROW_BYTES = 8,       /* device bytes of the stored rows */
+    PCT_STAT_BATCH_CTA = 9,       /* threads per CTA of the last batched solve */
+    PCT_STAT_BATCH_CTAS = 10,     /* CTAs of the last batched solve */
+    PCT_STAT_GRAPH_REPLAYS = 11   /* batched solves replayed from a CUDA graph */
 };
 
 /* Create a context on CUDA device `device`.
@@ -228,6 +247,23 @@ pct_status pct_build_rows(pct_ctx *ctx);
  * the result back and synchronizes. */
 pct_status pct_solve_host(pct_ctx *ctx, int32_t iters, float lambda, int64_t block_size,
                           float *x_host);
+
+/* Many independent DROP reconstructions (scans) in one persistent launch
+ * (Sec. IV-B per scan; the paper runs one scan per solver instance).  Scan k
+ * is the histories loaded in ctxs[k] (fused rows), solved in place into x[k]
+ * (device, that context's grid) with iters[k], lambda[k], block_size[k].
+ * CTAs are split between the scans in proportion to protons x iterations;
+ * the CTAs of a scan meet at a barrier after each block step and each apply;
+ * scans never wait for each other.  The launch is cooperative (all CTAs
+ * resident), its barrier waits are bounded (PCT_OPT_SPIN_LIMIT).  Options of
+ * ctxs[0] apply: PCT_OPT_GRAPH, PCT_OPT_AUTOTUNE, PCT_OPT_CTA_THREADS.  The
+ * work runs on an internal stream ordered after, and before, ctxs[0]'s
+ * stream; other contexts' streams are synchronized first.  Device errors and
+ * barrier timeouts are reported by pct_synchronize(ctxs[0]) (PCT_ERR_TIMEOUT).
+ * Errors: PCT_ERR_ARG (null, duplicate context, more scans than resident
+ * CTAs), PCT_ERR_STATE, PCT_ERR_OOM, PCT_ERR_CUDA. */
+pct_status pct_solve_batch(pct_ctx *const *ctxs, int32_t count, const int32_t *iters,
+                           const float *lambda, const int64_t *block_size, float *const *x);
 
 /* Wait for the context's stream; report asynchronous CUDA errors
  * (PCT_ERR_CUDA) and device-side check failures (PCT_ERR_DEVICE). */

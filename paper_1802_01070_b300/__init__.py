@@ -28,6 +28,8 @@ PCT_OK, PCT_ERR_ARG, PCT_ERR_CUDA, PCT_ERR_OOM, PCT_ERR_STATE, PCT_ERR_TIMEOUT, 
 STATUS_NAMES = {0: "PCT_OK", 1: "PCT_ERR_ARG", 2: "PCT_ERR_CUDA", 3: "PCT_ERR_OOM",
                 4: "PCT_ERR_STATE", 5: "PCT_ERR_TIMEOUT", 6: "PCT_ERR_DEVICE"}
 PCT_OPT_CTA_THREADS, PCT_OPT_MLP_STEP_UM, PCT_OPT_MEM_CAP_BYTES, PCT_OPT_TIMING, PCT_OPT_MODE = 1, 2, 3, 4, 5
+PCT_OPT_GRAPH, PCT_OPT_AUTOTUNE, PCT_OPT_SPIN_LIMIT, PCT_OPT_TEST_UNREACHABLE_BARRIER = 6, 7, 8, 9
+PCT_STAT_BATCH_CTA, PCT_STAT_BATCH_CTAS, PCT_STAT_GRAPH_REPLAYS = 9, 10, 11
 PCT_MODE_FUSED, PCT_MODE_CSR, PCT_MODE_PACKED = 0, 1, 2
 (PCT_STAT_LAUNCHES, PCT_STAT_FUSED_LAUNCHES, PCT_STAT_FUSED_MS, PCT_STAT_DEVICE_BYTES,
  PCT_STAT_N_PROTONS, PCT_STAT_N_HULL_VOXELS, PCT_STAT_ROW_ENTRIES, PCT_STAT_ROW_BYTES) = 1, 2, 3, 4, 5, 6, 7, 8
@@ -41,7 +43,8 @@ STATE_FIELDS = ("u_in", "u_out", "t0", "theta0", "v0", "psi0", "t2", "theta2", "
 EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct_get_option",
            "pct_load_histories", "pct_hull_states", "pct_mlp", "pct_rows", "pct_forward",
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
-           "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam")
+           "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam",
+           "pct_solve_batch")
 
 
 class PctError(RuntimeError):
@@ -87,6 +90,7 @@ def load_library(path: str = LIB_PATH):
         "pct_get_stat": ([P, I32, P], ctypes.c_int),
         "pct_reset_stats": ([P], ctypes.c_int),
         "pct_build_rows": ([P], ctypes.c_int),
+        "pct_solve_batch": ([P, I32, P, P, P, P], ctypes.c_int),
         "pct_tv": ([P, P, F, P, P], ctypes.c_int),
         "pct_adam": ([P, P, P, P, P, I64, F, F, F, F, I32], ctypes.c_int),
         "pct_solve_noalloc": ([P, P, I64, P, P, P, P, P, P, I32, F, I64, P, ctypes.c_int, P],
@@ -285,6 +289,25 @@ def pct_adam(ctx, x, grad, m, v, lr, beta1, beta2, eps, step):
                                         _dptr(m, torch.float32, n, "m"), _dptr(v, torch.float32, n, "v"),
                                         int(n), float(lr), float(beta1), float(beta2), float(eps),
                                         int(step)))
+
+
+def pct_solve_batch(contexts, iters, lams, blocks, xs):
+    """Batched DROP over several Contexts (one scan each), in one persistent launch.
+
+    contexts: list of Context; iters, lams, blocks: per-scan lists; xs: list of
+    CUDA float32 tensors, updated in place.  Ordered on the first context's stream.
+    """
+    import torch
+    k = len(contexts)
+    if not (len(iters) == len(lams) == len(blocks) == len(xs) == k) or k == 0:
+        raise ValueError("one iters, lambda, block and x per context")
+    H = (ctypes.c_void_p * k)(*[c.handle for c in contexts])
+    IT = (ctypes.c_int32 * k)(*[int(v) for v in iters])
+    LA = (ctypes.c_float * k)(*[float(v) for v in lams])
+    BL = (ctypes.c_int64 * k)(*[int(v) for v in blocks])
+    X = (ctypes.c_void_p * k)(*[_dptr(x, torch.float32, c.n_vox, "x").value for c, x in zip(contexts, xs)])
+    with _Ordered(contexts[0]):
+        _check(contexts[0].handle, load_library().pct_solve_batch(H, k, IT, LA, BL, X))
 
 
 def pct_build_rows(ctx):

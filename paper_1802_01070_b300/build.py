@@ -10,8 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libpct.so")
-SOURCES = ["pct_api.cu", "pct_kernels.cu", "pct_rows.cu", "pct_grad.cu", "pct_noalloc.cu"]
-HEADERS = ["pct_device.cuh", "pct_warp.cuh", "pct_internal.h"]
+SOURCES = ["pct_api.cu", "pct_kernels.cu", "pct_rows.cu", "pct_grad.cu", "pct_batch.cu", "pct_noalloc.cu"]
+HEADERS = ["pct_device.cuh", "pct_warp.cuh", "pct_internal.h", "pct_batch.h"]
 
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "pct.h"
+#include "pct_batch.h"
 #include "pct_internal.h"
 
 using namespace pct;
@@ -60,6 +61,21 @@ struct pct_ctx {
     std::unordered_map<void*, size_t> sizes;
     int64_t launches = 0;
     int64_t fused_launches = 0;
+    // batched solve (pct_solve_batch with this context first)
+    int graph = 0, autotune = 0, test_unreachable = 0;
+    int64_t spin_limit = 1 << 27;
+    int batch_cta = 0, batch_ctas = 0;
+    int64_t graph_replays = 0;
+    ScanDesc* d_scans = nullptr;
+    unsigned* d_bar = nullptr;
+    int* d_abort = nullptr;
+    int scan_cap = 0;
+    cudaStream_t batch_stream = nullptr;
+    cudaEvent_t batch_ev[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<int64_t> graph_key;
+    std::vector<std::vector<int64_t>> tuned_keys;
+    std::vector<int> tuned_cta;
     std::vector<cudaEvent_t> ev;   // pairs (start, stop) of timed fused launches
     size_t ev_used = 0;
     std::string err;
@@ -439,6 +455,10 @@ void pct_destroy(pct_ctx* c)
     for (auto& kv : c->sizes) cudaFree(kv.first);
     c->sizes.clear();
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    for (cudaEvent_t e : c->batch_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->batch_stream) cudaStreamDestroy(c->batch_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -473,6 +493,19 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
     case PCT_OPT_TIMING:
         c->timing = value ? 1 : 0;
         return PCT_OK;
+    case PCT_OPT_GRAPH:
+        c->graph = value ? 1 : 0;
+        return PCT_OK;
+    case PCT_OPT_AUTOTUNE:
+        c->autotune = value ? 1 : 0;
+        return PCT_OK;
+    case PCT_OPT_SPIN_LIMIT:
+        if (value < 1 || value > (int64_t)1 << 30) return fail(c, PCT_ERR_ARG, "spin limit must be 1..2^30");
+        c->spin_limit = value;
+        return PCT_OK;
+    case PCT_OPT_TEST_UNREACHABLE_BARRIER:
+        c->test_unreachable = value ? 1 : 0;
+        return PCT_OK;
     case PCT_OPT_MODE:
         if (value != PCT_MODE_FUSED && value != PCT_MODE_CSR && value != PCT_MODE_PACKED)
             return fail(c, PCT_ERR_ARG, "unknown mode");
@@ -493,6 +526,10 @@ pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
     case PCT_OPT_MEM_CAP_BYTES: *value = c->mem_cap; return PCT_OK;
     case PCT_OPT_TIMING: *value = c->timing; return PCT_OK;
     case PCT_OPT_MODE: *value = c->mode; return PCT_OK;
+    case PCT_OPT_GRAPH: *value = c->graph; return PCT_OK;
+    case PCT_OPT_AUTOTUNE: *value = c->autotune; return PCT_OK;
+    case PCT_OPT_SPIN_LIMIT: *value = c->spin_limit; return PCT_OK;
+    case PCT_OPT_TEST_UNREACHABLE_BARRIER: *value = c->test_unreachable; return PCT_OK;
     default: return PCT_ERR_ARG;
     }
 }
@@ -728,6 +765,235 @@ pct_status pct_solve_host(pct_ctx* c, int32_t iters, float lambda, int64_t block
     return pct_synchronize(c);
 }
 
+namespace {
+
+// Enqueue one batched solve on `stream`: clear barriers and accumulators,
+// prepare every scan's records, launch the persistent kernel.
+pct_status enqueue_batch(pct_ctx* c0, pct_ctx* const* ctxs, int32_t count, const std::vector<ScanDesc>& scans,
+                         int cta, int total, cudaStream_t stream, float* const* x)
+{
+    int64_t* launches = &c0->launches;
+    const Launch L0{stream, c0->cta, launches};
+    cudaError_t e = cudaMemsetAsync(c0->d_bar, 0, sizeof(unsigned) * count, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c0->d_abort, 0, sizeof(int) * count, stream);
+    for (int32_t k = 0; k < count && e == cudaSuccess; ++k) {
+        pct_ctx* c = ctxs[k];
+        if (c->n == 0) continue;
+        const Launch L{stream, c->cta, launches};
+        e = launch_prepare(L, geo_of(c), c->d_hist, c->stride, c->n, c->d_rec);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_acc, 0, (size_t)c->n_vox * sizeof(float2), stream);
+    }
+    (void)x;
+    if (e == cudaSuccess)
+        e = launch_drop_batch(L0, c0->d_scans, count, total, cta, c0->d_flags, (int)c0->spin_limit,
+                              c0->test_unreachable);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c0, e, "batched solve");
+}
+
+}  // namespace
+
+pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* iters, const float* lambda,
+                           const int64_t* block_size, float* const* x)
+{
+    if (!ctxs || count < 1 || !ctxs[0] || !iters || !lambda || !block_size || !x) return PCT_ERR_ARG;
+    pct_ctx* c0 = ctxs[0];
+    if (count > 4096) return fail(c0, PCT_ERR_ARG, "at most 4096 scans per batch");
+    DeviceGuard dg(c0->device);
+    int64_t work_total = 0;
+    for (int32_t k = 0; k < count; ++k) {
+        pct_ctx* c = ctxs[k];
+        if (!c || !x[k]) return fail(c0, PCT_ERR_ARG, "null context or x in the batch");
+        if (c->device != c0->device) return fail(c0, PCT_ERR_ARG, "batch contexts on different devices");
+        if (!c->loaded) return fail(c0, PCT_ERR_STATE, "a batch context has no histories");
+        if (iters[k] < 0 || block_size[k] < 1 || !std::isfinite(lambda[k]))
+            return fail(c0, PCT_ERR_ARG, "batch iters < 0, block size < 1 or non-finite lambda");
+        for (int32_t q = 0; q < k; ++q)
+            if (ctxs[q] == c) return fail(c0, PCT_ERR_ARG, "a context appears twice in the batch");
+        pct_status s = ensure_acc(c);
+        if (s != PCT_OK) return fail(c0, s, "batch accumulator: " + c->err);
+        work_total += c->n * (int64_t)iters[k];
+    }
+    // other contexts' pending work comes first
+    for (int32_t k = 1; k < count; ++k)
+        if (ctxs[k]->stream != c0->stream) cudaStreamSynchronize(ctxs[k]->stream);
+    if (count > c0->scan_cap) {
+        dfree(c0, c0->d_scans);
+        dfree(c0, c0->d_bar);
+        dfree(c0, c0->d_abort);
+        c0->d_scans = nullptr;
+        c0->d_bar = nullptr;
+        c0->d_abort = nullptr;
+        c0->scan_cap = 0;
+        void* p = nullptr;
+        pct_status s = dalloc(c0, &p, sizeof(ScanDesc) * count, "batch descriptors");
+        if (s != PCT_OK) return s;
+        c0->d_scans = (ScanDesc*)p;
+        if ((s = dalloc(c0, &p, sizeof(unsigned) * count, "batch barriers")) != PCT_OK) return s;
+        c0->d_bar = (unsigned*)p;
+        if ((s = dalloc(c0, &p, sizeof(int) * count, "batch abort flags")) != PCT_OK) return s;
+        c0->d_abort = (int*)p;
+        c0->scan_cap = count;
+    }
+    if (!c0->batch_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c0->batch_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c0->batch_ev[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c0->batch_ev[1], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(c0, e, "batch stream");
+    }
+    // CTA size: autotuned (fastest of 128 / 256 threads on one iteration, on
+    // scratch copies of x), or the context's CTA option
+    // what the tuned CTA size and the captured graph depend on (x pointers and
+    // lambda live in the descriptors, uploaded before every launch)
+    std::vector<int64_t> key;
+    for (int32_t k = 0; k < count; ++k) {
+        key.push_back((int64_t)(intptr_t)ctxs[k]);
+        key.push_back(iters[k]);
+        key.push_back(block_size[k]);
+        key.push_back(ctxs[k]->n);
+    }
+    int cta = c0->cta;
+    auto build_scans = [&](int cta_try, int* total_out, std::vector<ScanDesc>& scans,
+                           float* const* xs, const int32_t* its) -> pct_status {
+        int cap = 0;
+        cudaError_t e = batch_max_ctas(cta_try, c0->device, &cap);
+        if (e != cudaSuccess) return cuda_fail(c0, e, "batch occupancy");
+        if (cap < count) return fail(c0, PCT_ERR_ARG, "more scans than co-resident CTAs");
+        scans.assign(count, ScanDesc{});
+        int used = 0;
+        int64_t work_left = 0;
+        for (int32_t k = 0; k < count; ++k) work_left += ctxs[k]->n * (int64_t)its[k];
+        for (int32_t k = 0; k < count; ++k) {
+            pct_ctx* c = ctxs[k];
+            ScanDesc& d = scans[k];
+            const Geo G = geo_of(c);
+            d.g = G.g;
+            d.mc = G.mc;
+            d.mask = c->d_mask;
+            d.rec = c->d_rec;
+            d.stride = c->stride;
+            d.n = c->n;
+            d.x = xs[k];
+            d.acc = c->d_acc;
+            d.n_vox = c->n_vox;
+            d.iters = its[k];
+            d.lambda = lambda[k];
+            d.block = block_size[k];
+            // CTAs in proportion to work, at least one each
+            const int64_t wk = c->n * (int64_t)its[k];
+            const int left = cap - used - (count - 1 - k);
+            int share = work_left > 0 ? (int)((double)wk / (double)work_left * (cap - used)) : 1;
+            if (share < 1) share = 1;
+            if (share > left) share = left;
+            work_left -= wk;
+            d.cta0 = used;
+            d.ncta = share;
+            d.bar = c0->d_bar + k;
+            d.abort = c0->d_abort + k;
+            used += share;
+        }
+        *total_out = used;
+        return PCT_OK;
+    };
+    cudaStream_t bs = c0->batch_stream;
+    cudaError_t e = cudaEventRecord(c0->batch_ev[0], c0->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, c0->batch_ev[0], 0);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "batch ordering");
+    if (c0->autotune) {
+        size_t hit = c0->tuned_keys.size();
+        for (size_t q = 0; q < c0->tuned_keys.size(); ++q)
+            if (c0->tuned_keys[q] == key) hit = q;
+        if (hit < c0->tuned_keys.size()) {
+            cta = c0->tuned_cta[hit];
+        } else {
+            // time each candidate on one iteration over scratch copies of x
+            std::vector<float*> tmp(count, nullptr);
+            pct_status s = PCT_OK;
+            for (int32_t k = 0; k < count && s == PCT_OK; ++k) {
+                void* p = nullptr;
+                s = dalloc(c0, &p, (size_t)ctxs[k]->n_vox * sizeof(float), "autotune scratch");
+                tmp[k] = (float*)p;
+            }
+            std::vector<int32_t> one(count, 1);
+            float best = 1e30f;
+            int best_cta = cta;
+            cudaEvent_t t0 = nullptr, t1 = nullptr;
+            cudaEventCreate(&t0);
+            cudaEventCreate(&t1);
+            for (int cand : {128, 256}) {
+                if (s != PCT_OK) break;
+                std::vector<ScanDesc> scans;
+                int total = 0;
+                if ((s = build_scans(cand, &total, scans, tmp.data(), one.data())) != PCT_OK) break;
+                for (int32_t k = 0; k < count; ++k)
+                    cudaMemcpyAsync(tmp[k], x[k], (size_t)ctxs[k]->n_vox * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, bs);
+                cudaMemcpyAsync(c0->d_scans, scans.data(), sizeof(ScanDesc) * count, cudaMemcpyHostToDevice, bs);
+                cudaEventRecord(t0, bs);
+                s = enqueue_batch(c0, ctxs, count, scans, cand, total, bs, tmp.data());
+                cudaEventRecord(t1, bs);
+                cudaStreamSynchronize(bs);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, t0, t1);
+                if (s == PCT_OK && ms < best) {
+                    best = ms;
+                    best_cta = cand;
+                }
+            }
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            for (float* p : tmp) dfree(c0, p);
+            if (s != PCT_OK) return s;
+            cta = best_cta;
+            c0->tuned_keys.push_back(key);
+            c0->tuned_cta.push_back(cta);
+        }
+    }
+    key.push_back(cta);
+    std::vector<ScanDesc> scans;
+    int total = 0;
+    pct_status s = build_scans(cta, &total, scans, x, iters);
+    if (s != PCT_OK) return s;
+    c0->batch_cta = cta;
+    c0->batch_ctas = total;
+    // descriptors change only with the batch; upload them outside any graph
+    e = cudaMemcpyAsync(c0->d_scans, scans.data(), sizeof(ScanDesc) * count, cudaMemcpyHostToDevice, bs);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
+    if (e != cudaSuccess) return cuda_fail(c0, e, "batch descriptors");
+    if (c0->graph) {
+        if (!c0->graph_exec || c0->graph_key != key) {
+            if (c0->graph_exec) cudaGraphExecDestroy(c0->graph_exec);
+            c0->graph_exec = nullptr;
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(c0, e, "graph capture");
+            s = enqueue_batch(c0, ctxs, count, scans, cta, total, bs, x);
+            cudaError_t e2 = cudaStreamEndCapture(bs, &g);
+            if (s != PCT_OK) {
+                if (g) cudaGraphDestroy(g);
+                return s;
+            }
+            if (e2 != cudaSuccess) return cuda_fail(c0, e2, "graph capture");
+            e = cudaGraphInstantiate(&c0->graph_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c0->graph_exec = nullptr;
+                return cuda_fail(c0, e, "graph instantiate");
+            }
+            c0->graph_key = key;
+        }
+        e = cudaGraphLaunch(c0->graph_exec, bs);
+        if (e != cudaSuccess) return cuda_fail(c0, e, "graph launch");
+        ++c0->graph_replays;
+        c0->launches += 1 + count;
+    } else {
+        s = enqueue_batch(c0, ctxs, count, scans, cta, total, bs, x);
+        if (s != PCT_OK) return s;
+    }
+    e = cudaEventRecord(c0->batch_ev[1], bs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c0->stream, c0->batch_ev[1], 0);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c0, e, "batch ordering");
+}
+
 pct_status pct_synchronize(pct_ctx* c)
 {
     if (!c) return PCT_ERR_ARG;
@@ -740,6 +1006,8 @@ pct_status pct_synchronize(pct_ctx* c)
     if (e != cudaSuccess) return cuda_fail(c, e, "flag read");
     if (flags) {
         cudaMemset(c->d_flags, 0, sizeof(unsigned));
+        if (flags & kFlagBarrierTimeout)
+            return fail(c, PCT_ERR_TIMEOUT, "a batched-solve barrier wait gave up (spin limit reached)");
         std::string m = "device check failed:";
         if (flags & kFlagWalkGuard) m += " voxel walk step bound exceeded;";
         if (flags & kFlagHullGuard) m += " hull search step bound exceeded;";
@@ -776,6 +1044,9 @@ pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
     case PCT_STAT_N_HULL_VOXELS: *value = (double)c->n_hull; return PCT_OK;
     case PCT_STAT_ROW_ENTRIES: *value = (double)c->nnz; return PCT_OK;
     case PCT_STAT_ROW_BYTES: *value = (double)row_bytes(c); return PCT_OK;
+    case PCT_STAT_BATCH_CTA: *value = (double)c->batch_cta; return PCT_OK;
+    case PCT_STAT_BATCH_CTAS: *value = (double)c->batch_ctas; return PCT_OK;
+    case PCT_STAT_GRAPH_REPLAYS: *value = (double)c->graph_replays; return PCT_OK;
     default: return fail(c, PCT_ERR_ARG, "unknown stat key");
     }
 }

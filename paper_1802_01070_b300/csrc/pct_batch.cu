@@ -1,0 +1,146 @@
+// pct_batch.cu -- many independent DROP reconstructions (scans) in one
+// persistent cooperative launch.
+//
+// Each scan owns a contiguous range of CTAs, sized in proportion to its work
+// (protons x iterations).  The CTAs of a scan run the scan's DROP blocks in
+// order (Sec. IV-B): one warp per proton for the block step, a barrier among
+// the scan's CTAs, the block apply, another barrier.  Scans never wait on each
+// other.  The launch is cooperative, so all CTAs are resident together and the
+// per-scan barriers cannot wait for a CTA that is not running.  Every barrier
+// wait is bounded: after `spin_limit` polls the waiting CTA sets a flag, marks
+// the scan aborted and returns, so a lost arrival ends the kernel with an error
+// instead of hanging it.
+//
+// x and the accumulator are rewritten inside the launch by other CTAs, so they
+// are read through L2 only (ld.global.cg) and written back the same way.
+#include "pct_batch.h"
+#include "pct_warp.cuh"
+
+namespace pct {
+
+namespace {
+
+constexpr int kBatchRunSlots = 24;
+
+__device__ __forceinline__ bool scan_barrier(const ScanDesc& d, int* abort_flag, unsigned* flags,
+                                             int spin_limit, int extra_target)
+{
+    __shared__ int ok;   // one decision for the whole CTA
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned old = atomicAdd(d.bar, 1u);
+        const unsigned target = (old / (unsigned)d.ncta + 1u) * (unsigned)d.ncta + (unsigned)extra_target;
+        int spins = 0;
+        while (true) {
+            const unsigned now = *(volatile unsigned*)d.bar;
+            if (now >= target) break;
+            if (*(volatile int*)abort_flag) break;
+            if (++spins > spin_limit) {
+                atomicOr(flags, kFlagBarrierTimeout);
+                atomicExch(abort_flag, 1);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+        ok = *(volatile int*)abort_flag == 0;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+__global__ void __launch_bounds__(256, 4)
+k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int spin_limit,
+             int test_unreachable)
+{
+    extern __shared__ unsigned char smem[];
+    int s = 0;
+    while (s + 1 < nscan && (int)blockIdx.x >= scans[s + 1].cta0) ++s;
+    const ScanDesc d = scans[s];
+    if ((int)blockIdx.x >= d.cta0 + d.ncta) return;   // spare CTA beyond the last scan
+    int* abort_flag = d.abort;
+    const int warps = blockDim.x >> 5;
+    const int warp_in_scan = ((int)blockIdx.x - d.cta0) * warps + (threadIdx.x >> 5);
+    const int nwarp = d.ncta * warps;
+    const int tid_in_scan = ((int)blockIdx.x - d.cta0) * blockDim.x + threadIdx.x;
+    const int nthr = d.ncta * blockDim.x;
+    unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * kBatchRunSlots * kWarp * 8;
+    const RunSlots slots{(int*)base, (float*)(base + (size_t)kBatchRunSlots * kWarp * 4)};
+    const RecView rv{d.rec, d.stride};
+    // only the first barrier of scan 0 is made unreachable by the test option
+    int extra = (test_unreachable && s == 0) ? 1 : 0;
+    for (int it = 0; it < d.iters; ++it) {
+        for (int64_t first = 0; first < d.n; first += d.block) {
+            const int64_t count = d.block < d.n - first ? d.block : d.n - first;
+            for (int64_t p = warp_in_scan; p < count; p += nwarp) {
+                const int64_t i = first + p;
+                Path P;
+                if (!load_path(rv, i, d.mc, P)) continue;
+                LaneWalk w;
+                float sv, q;
+                warp_walk<kBatchRunSlots, true, true>(P, d.mc, d.g, d.mask, d.x, flags, slots, d.mc.cmin,
+                                                      w, sv, q);
+                if (!(q > 0.f)) continue;
+                const float r = (rv.get(R_B, i) - sv) / q;
+                float2* acc = d.acc;
+                replay_runs<kBatchRunSlots>(P, d.mc, d.g, d.mask, flags, slots, w, [&](int j, float l) {
+                    atomicAdd(acc + j, make_float2(l * r, 1.f));
+                });
+            }
+            if (!scan_barrier(d, abort_flag, flags, spin_limit, extra)) return;
+            extra = 0;
+            for (int64_t j = tid_in_scan; j < d.n_vox; j += nthr) {
+                const float2 a = __ldcg(d.acc + j);
+                if (a.y > 0.f) {
+                    __stcg(d.x + j, fmaf(d.lambda, a.x / a.y, __ldcg(d.x + j)));
+                    __stcg(d.acc + j, make_float2(0.f, 0.f));
+                }
+            }
+            if (!scan_barrier(d, abort_flag, flags, spin_limit, 0)) return;
+        }
+    }
+}
+
+}  // namespace
+
+size_t batch_smem(int cta)
+{
+    return (size_t)(cta / kWarp) * kBatchRunSlots * kWarp * 8;
+}
+
+cudaError_t batch_max_ctas(int cta, int device, int* out)
+{
+    int per_sm = 0, sms = 0;
+    cudaError_t e = cudaFuncSetAttribute(k_drop_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batch_smem(256));
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_drop_batch, cta, batch_smem(cta));
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) return e;
+    *out = per_sm * sms;
+    return cudaSuccess;
+}
+
+cudaError_t launch_drop_batch(const Launch& L, const ScanDesc* scans_dev, int nscan, int total_ctas,
+                              int cta, unsigned* flags, int spin_limit, int test_unreachable)
+{
+    void* args[] = {(void*)&scans_dev, (void*)&nscan, (void*)&flags, (void*)&spin_limit,
+                    (void*)&test_unreachable};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)total_ctas);
+    cfg.blockDim = dim3((unsigned)cta);
+    cfg.dynamicSmemBytes = batch_smem(cta);
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_drop_batch, args);
+    ++*L.launches;
+    return e;
+}
+
+}  // namespace pct

@@ -150,7 +150,9 @@ struct Dims {
     __device__ __forceinline__ int index(int ix, int iy, int iz) const { return ix + nx * (iy + ny * iz); }
 };
 
-template <int RL, bool DOT>
+// CG: read x through L2 only (ld.global.cg), for kernels in which other CTAs
+// rewrite x between barriers; otherwise the read-only cache path.
+template <int RL, bool DOT, bool CG = false>
 struct StoreSink {
     Dims g;
     const uint8_t* __restrict__ mask;
@@ -193,7 +195,7 @@ struct StoreSink {
         if (g.inside(ix, iy, iz)) {
             j = g.index(ix, iy, iz);
             m = __ldg(mask + j);
-            if (DOT) xv = __ldg(x + j);
+            if (DOT) xv = CG ? __ldcg(x + j) : __ldg(x + j);
         }
         commit();
         pj = j;
@@ -216,7 +218,7 @@ __device__ __forceinline__ void lane_range(const Path& P, int cmin, int lane, in
 // Pass 1 for the proton P on the calling warp: walk, store, accumulate, and
 // resolve the runs shared by neighbouring lanes.  Returns the warp-reduced
 // (s, q) on every lane.
-template <int RL, bool DOT>
+template <int RL, bool DOT, bool CG = false>
 __device__ __forceinline__ void warp_walk(const Path& P, const MlpC& mc, const GridC& g,
                                           const uint8_t* __restrict__ mask,
                                           const float* __restrict__ x, unsigned* flags,
@@ -233,7 +235,7 @@ __device__ __forceinline__ void warp_walk(const Path& P, const MlpC& mc, const G
     w.s = w.q = 0.f;
     w.ends = range_ends(P, mc, g, w.k0, w.k1);
     if (w.k0 < w.k1) {
-        StoreSink<RL, DOT> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, lane, &w, -1, 0.f, 0.f, 0, false};
+        StoreSink<RL, DOT, CG> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, lane, &w, -1, 0.f, 0.f, 0, false};
         walk_points(P, mc, g, flags, w.k0, w.k1, w.ends, sink);
         sink.commit();
     }

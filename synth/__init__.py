@@ -82,6 +82,22 @@ CONFIGS = {
 }
 
 
+def validation_scans(count: int = 16, n_min: float = 1e5, n_max: float = 2e6, seed_offset: int = 10):
+    """Small scans of uneven size for batched solves: proton counts log-uniform
+    in [n_min, n_max], grids between 64x64x8 and 128x128x32 (1 mm), seeded
+    ellipsoid phantoms, 90 angles, 6 DROP iterations, block 3200."""
+    g = torch.Generator().manual_seed(SEED_BASE + seed_offset)
+    out = []
+    for k in range(count):
+        u = torch.rand(3, generator=g, dtype=torch.float64)
+        n = int(round(math.exp(math.log(n_min) + (math.log(n_max) - math.log(n_min)) * u[0].item())))
+        nx = (64, 96, 128)[int(u[1].item() * 3) % 3]
+        nz = (8, 16, 32)[int(u[2].item() * 3) % 3]
+        out.append(ScanConfig("scan%02d" % k, (nx, nx, nz), 1.0, "ellipsoids", n, 90, 6, 0.5, 3200,
+                              seed_offset=seed_offset + 1 + k))
+    return out
+
+
 def scaled(cfg: ScanConfig, n_protons: int, name: str | None = None, **kw) -> ScanConfig:
     """A copy of ``cfg`` with another proton count (same phantom, beam and seed)."""
     d = dict(cfg.__dict__)
