@@ -13,8 +13,11 @@ LIB = os.path.join(PKG, "libpct.so")
 SOURCES = ["pct_api.cu", "pct_kernels.cu", "pct_rows.cu", "pct_grad.cu", "pct_batch.cu", "pct_noalloc.cu"]
 HEADERS = ["pct_device.cuh", "pct_warp.cuh", "pct_internal.h", "pct_batch.h"]
 
+# --fmad=false: no implicit contraction of a*b+c, so every kernel that walks a
+# path (fused solve, stored-row builds, row dump, batch) computes bit-identical
+# MLP points; fused multiply-adds are written out with fmaf where wanted.
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
-              "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
+              "--fmad=false", "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
 
 
 def _nvcc():

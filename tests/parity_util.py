@@ -120,3 +120,28 @@ def solve_parity(xg, xo, hull, diff_vox):
     clean = hm & ~diff_vox
     return (float(rel[clean].max()) if clean.any() else 0.0, int((hm & diff_vox).sum()),
             float(rel[hm].max()), float((rel[hm] <= 1e-3).mean()))
+
+
+def chord_diff_voxels(gidx, glen, gnnz, rowptr_o, j_o, ln_o, n_vox, tol=CHORD_TOL_MM):
+    """Voxels crossed by a row whose GPU and oracle chords differ by more than
+    tol (a grazing crossing resolved differently in FP32 and FP64), or by a
+    row whose voxel sequence differs."""
+    m = gnnz.shape[0]
+    out = np.zeros(n_vox, bool)
+    for i in range(m):
+        a, b = rowptr_o[i], rowptr_o[i + 1]
+        k = int(gnnz[i])
+        gj, gl = gidx[i, :k], glen[i, :k]
+        oj, ol = j_o[a:b], ln_o[a:b]
+        if k == oj.size and np.array_equal(gj, oj):
+            bad = np.abs(gl - ol) > tol
+            out[oj[bad]] = True
+        else:
+            # sequences differ (near-face row): flag voxels whose chord sum differs
+            vox = np.union1d(gj, oj)
+            sg = np.zeros(vox.size)
+            so = np.zeros(vox.size)
+            np.add.at(sg, np.searchsorted(vox, gj), gl)
+            np.add.at(so, np.searchsorted(vox, oj), ol)
+            out[vox[np.abs(sg - so) > tol]] = True
+    return out
