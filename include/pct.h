@@ -135,6 +135,8 @@ enum pct_stat {
  * The hull is not part of the paper; the reading used is that a proton's path
  * starts where its straight entry tracker line first enters a hull voxel and
  * ends where its straight exit tracker line, followed backwards, first does.
+ * The context keeps the mask and, for that search, the chessboard distance of
+ * every voxel to the hull (one byte per voxel each), built on the GPU here.
  * Errors: PCT_ERR_ARG (null out/grid, non-positive sizes, grid over 2^31
  * voxels), PCT_ERR_CUDA, PCT_ERR_OOM. */
 pct_status pct_create(pct_ctx **out, const pct_grid *grid, const uint8_t *hull_mask, int device,
@@ -177,6 +179,15 @@ pct_status pct_load_histories(pct_ctx *ctx, int64_t n, const float *const in_xyz
  * entry and exit, mm), t0, theta0, v0, psi0 (entry state), t2, theta2, v2, psi2
  * (exit state), valid (1.0 / 0.0), spare.  Errors: PCT_ERR_ARG, PCT_ERR_STATE. */
 pct_status pct_hull_states(pct_ctx *ctx, int64_t first, int64_t count, float *out_states);
+
+/* Copy of the context's hull distance map (device out, nx*ny*nz bytes, x
+ * fastest): per voxel the chessboard distance max(|dx|, |dy|, |dz|), in
+ * voxels, to the nearest hull voxel, capped at 255; 0 inside the hull, 255
+ * everywhere when the hull is empty.  The hull search of every path start
+ * skips empty space with it.  Not part of the paper: the hull itself is a
+ * reading (see pct_create).  Asynchronous on the context's stream.
+ * Errors: PCT_ERR_ARG (null ctx or out), PCT_ERR_CUDA. */
+pct_status pct_hull_distance(pct_ctx *ctx, uint8_t *out_dist);
 
 /* MLP polylines of protons [first, first+count) (Sec. I, most likely path):
  * the hull entry point, the MLP at depths u_in + k*du (k >= 1, below u_out by
@@ -282,9 +293,10 @@ pct_status pct_reset_stats(pct_ctx *ctx);
  * It computes what pct_create + pct_load_histories + pct_solve compute (same
  * kernels, MLP spacing = smallest voxel edge), but takes every input as a
  * device pointer and keeps all scratch (a copy of the histories, the
- * per-proton records, the per-voxel DROP accumulator, the MLP table) in fixed
- * device arrays compiled into the library: about 15 MB, held on every GPU that
- * loads the library until the process exits.  Limits: at most
+ * per-proton records, the per-voxel DROP accumulator, the hull distance map
+ * of the hull search and its scratch, the MLP table) in fixed device arrays
+ * compiled into the library: about 18 MB, held on every GPU that loads the
+ * library until the process exits.  Limits: at most
  * PCT_NOALLOC_MAX_PROTONS protons, PCT_NOALLOC_MAX_VOXELS voxels, and a grid
  * diagonal of at most PCT_NOALLOC_MAX_SAMPLES MLP steps; larger inputs are
  * rejected with PCT_ERR_ARG before any GPU work.

@@ -44,7 +44,7 @@ EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct
            "pct_load_histories", "pct_hull_states", "pct_mlp", "pct_rows", "pct_forward",
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
            "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam",
-           "pct_solve_batch")
+           "pct_solve_batch", "pct_hull_distance")
 
 
 class PctError(RuntimeError):
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
         "pct_get_option": ([P, I32, P], ctypes.c_int),
         "pct_load_histories": ([P, I64, P, P, P, P, P, P, ctypes.c_int], ctypes.c_int),
         "pct_hull_states": ([P, I64, I64, P], ctypes.c_int),
+        "pct_hull_distance": ([P, P], ctypes.c_int),
         "pct_mlp": ([P, I64, I64, I32, P, P], ctypes.c_int),
         "pct_rows": ([P, I64, I64, I32, P, P, P], ctypes.c_int),
         "pct_forward": ([P, P, P], ctypes.c_int),
@@ -197,6 +198,11 @@ def pct_hull_states(ctx, first, count, out):
     import torch
     _check(ctx, load_library().pct_hull_states(ctx, int(first), int(count),
                                                _dptr(out, torch.float32, 12 * count, "out")))
+
+
+def pct_hull_distance(ctx, n_vox, out):
+    import torch
+    _check(ctx, load_library().pct_hull_distance(ctx, _dptr(out, torch.uint8, n_vox, "out")))
 
 
 def pct_mlp(ctx, first, count, max_pts, out_xyz, out_npts):
@@ -423,6 +429,14 @@ class Context:
         with _Ordered(self):
             pct_hull_states(self._h, first, count, out)
         return out[:count * 12].view(count, 12)
+
+    def hull_distance(self):
+        """Chessboard distance of every voxel to the hull (uint8, nz x ny x nx)."""
+        import torch
+        out = torch.empty(self.n_vox, dtype=torch.uint8, device=self.device)
+        with _Ordered(self):
+            pct_hull_distance(self._h, self.n_vox, out)
+        return out.view(self.shape[2], self.shape[1], self.shape[0])
 
     def mlp(self, first=0, count=None, max_pts=512):
         import torch

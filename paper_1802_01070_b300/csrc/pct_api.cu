@@ -34,6 +34,7 @@ struct pct_ctx {
     int64_t n_vox = 0;
     int64_t n_hull = 0;
     uint8_t* d_mask = nullptr;
+    uint8_t* d_dist = nullptr;   // chessboard distance to the hull (hull search skipping)
     float4* d_sig1 = nullptr;
     int kmax = 0;
     int64_t du_um = 0;
@@ -204,6 +205,7 @@ Geo geo_of(const pct_ctx* c)
                                   (double)c->grid.dz * c->grid.dz);
     G.mc.cmin = (int)std::floor(diag / du) + 1;
     G.mask = c->d_mask;
+    G.dist = c->d_dist;
     G.flags = c->d_flags;
     return G;
 }
@@ -432,6 +434,16 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const uint8_t* hull_m
         e = cudaMemcpy(c->d_mask, mask.data(), (size_t)n_vox, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) s = cuda_fail(c, e, "hull mask upload");
     }
+    if (s == PCT_OK && (s = dalloc(c, &p, (size_t)n_vox, "hull distance map")) == PCT_OK) {
+        c->d_dist = (uint8_t*)p;
+        void* tmp = nullptr;
+        if ((s = dalloc(c, &tmp, (size_t)n_vox, "hull distance scratch")) == PCT_OK) {
+            e = launch_hull_dist(launch_of(c), c->d_mask, G.nx, G.ny, G.nz, (uint8_t*)tmp, c->d_dist);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) s = cuda_fail(c, e, "hull distance map");
+            dfree(c, tmp);
+        }
+    }
     if (s == PCT_OK && (s = dalloc(c, &p, sizeof(unsigned), "flags")) == PCT_OK) {
         c->d_flags = (unsigned*)p;
         e = cudaMemset(c->d_flags, 0, sizeof(unsigned));
@@ -603,6 +615,15 @@ pct_status pct_hull_states(pct_ctx* c, int64_t first, int64_t count, float* out)
     if (s != PCT_OK) return s;
     cudaError_t e = launch_hull_states(launch_of(c), c->d_rec, c->stride, first, count, out);
     return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "hull states");
+}
+
+pct_status pct_hull_distance(pct_ctx* c, uint8_t* out)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!out) return fail(c, PCT_ERR_ARG, "null output");
+    DeviceGuard dg(c->device);
+    cudaError_t e = cudaMemcpyAsync(out, c->d_dist, (size_t)c->n_vox, cudaMemcpyDeviceToDevice, c->stream);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "hull distance copy");
 }
 
 pct_status pct_mlp(pct_ctx* c, int64_t first, int64_t count, int32_t max_pts, float* out_xyz,

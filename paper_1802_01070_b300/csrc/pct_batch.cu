@@ -50,7 +50,7 @@ __device__ __forceinline__ bool scan_barrier(const ScanDesc& d, int* abort_flag,
     return ok != 0;
 }
 
-__global__ void __launch_bounds__(256, 4)
+__global__ void __launch_bounds__(256, 3)
 k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int spin_limit,
              int test_unreachable)
 {

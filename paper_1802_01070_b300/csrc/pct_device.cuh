@@ -152,7 +152,7 @@ __device__ __forceinline__ void mlp_offset(const Path& P, const MlpC& mc, int k,
     const float M11 = s1.z + T11;
     const float g0 = fmaf(W, s1.y, s1.x);
     const float g1 = s1.y;
-    const float rdet = __frcp_rn(fmaf(M00, M11, -M01 * M01));
+    const float rdet = __fdividef(1.f, fmaf(M00, M11, -M01 * M01));
     const float G0 = fmaf(g0, M11, -g1 * M01) * rdet;           // dimensionless
     const float G1 = fmaf(g1, M00, -g0 * M01) * rdet * 10.f;    // mm per rad
     dt = fmaf(w_mm, P.th0, fmaf(G0, P.d0t, G1 * P.d1t));
@@ -212,7 +212,17 @@ __device__ __forceinline__ int lin(const GridC& g, int ix, int iy, int iz)
 // that voxel (s_hit = 0).  The caller re-evaluates the crossing parameter from
 // them in FP64: for a line nearly parallel to the plane the FP32 parameter is
 // ill-conditioned.
+//
+// Empty-space skipping: `dist` (optional) holds, per voxel, the chessboard
+// distance d to the nearest hull voxel (0 inside the hull, capped at 255).
+// Every voxel within chessboard distance d-1 of a voxel at distance d is
+// outside the hull, so from a point of that voxel the line can advance until it
+// has moved d-1 voxels along its dominant axis without passing a hull voxel.
+// The jump keeps 1/16 voxel of slack for rounding and always ends in a voxel
+// outside the hull, so the hull voxel is still entered by a DDA step that sets
+// (axis, face).  Without `dist` the search visits every voxel.
 __device__ __forceinline__ bool hull_entry(const GridC& g, const uint8_t* __restrict__ mask,
+                                           const uint8_t* __restrict__ dist,
                                            float Tx, float Ty, float Tz, float Dx, float Dy,
                                            float Dz, float S, unsigned* flags, float& s_hit,
                                            int& axis, int& face)
@@ -253,9 +263,28 @@ __device__ __forceinline__ bool hull_entry(const GridC& g, const uint8_t* __rest
         iv[a] = k;
     }
     float s_cur = s_lo;
+    const float inv_dmax = 1.f / fmaxf(fabsf(Dx), fmaxf(fabsf(Dy), fabsf(Dz)));
     const int guard = g.nx + g.ny + g.nz + 4;
     for (int it = 0; it <= guard; ++it) {
-        if (__ldg(mask + lin(g, iv[0], iv[1], iv[2]))) {
+        const int j = lin(g, iv[0], iv[1], iv[2]);
+        if (dist) {
+            const int d = __ldg(dist + j);
+            if (d == 0) {
+                s_hit = s_cur;
+                return true;
+            }
+            if (d >= 2) {
+                const float s_jump = fmaf((float)d - 1.0625f, inv_dmax, s_cur);
+                if (!(s_jump < s_hi)) return false;
+                s_cur = s_jump;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    int k = start_index(fmaf(s_jump, D[a], T[a]), D[a]);
+                    iv[a] = k < 0 ? 0 : (k > n[a] - 1 ? n[a] - 1 : k);
+                }
+                continue;
+            }
+        } else if (__ldg(mask + j)) {
             s_hit = s_cur;
             return true;
         }

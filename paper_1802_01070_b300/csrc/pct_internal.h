@@ -24,9 +24,14 @@ struct Geo {
     GridC g;
     MlpC mc;
     const uint8_t* mask;  // device, nx*ny*nz bytes
+    const uint8_t* dist;  // device, nx*ny*nz bytes: chessboard distance to the hull (or null)
     unsigned* flags;      // device error word
 };
 
+// dist = chessboard distance of each voxel to the nearest hull voxel (capped at
+// 255); tmp is scratch of the same size.
+cudaError_t launch_hull_dist(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, uint8_t* tmp,
+                             uint8_t* dist);
 cudaError_t launch_prepare(const Launch& L, const Geo& G, const float* hist, int64_t stride,
                            int64_t n, float* rec);
 cudaError_t launch_hull_states(const Launch& L, const float* rec, int64_t stride, int64_t first,

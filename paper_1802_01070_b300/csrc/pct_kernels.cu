@@ -34,7 +34,8 @@ __device__ __forceinline__ double plane_crossing(const GridC& g, const double T[
 }
 
 __global__ void __launch_bounds__(kMaxCta)
-k_prepare(GridC g, const uint8_t* __restrict__ mask, unsigned* flags, const float* __restrict__ h,
+k_prepare(GridC g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ dist, unsigned* flags,
+          const float* __restrict__ h,
           int64_t stride, int64_t first, int64_t count, float* __restrict__ rec, float Lmax)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -61,8 +62,8 @@ k_prepare(GridC g, const uint8_t* __restrict__ mask, unsigned* flags, const floa
     const float Dox = -fmaf(-tto, s, c) * g.idx, Doy = -fmaf(tto, c, s) * g.idy, Doz = -tpo * g.idz;
     float s_in = 0.f, s_out = 0.f;
     int ax_in = -1, f_in = 0, ax_out = -1, f_out = 0;
-    if (ok) ok = hull_entry(g, mask, Tix, Tiy, Tiz, Dix, Diy, Diz, S, flags, s_in, ax_in, f_in);
-    if (ok) ok = hull_entry(g, mask, Tox, Toy, Toz, Dox, Doy, Doz, S, flags, s_out, ax_out, f_out);
+    if (ok) ok = hull_entry(g, mask, dist, Tix, Tiy, Tiz, Dix, Diy, Diz, S, flags, s_in, ax_in, f_in);
+    if (ok) ok = hull_entry(g, mask, dist, Tox, Toy, Toz, Dox, Doy, Doz, S, flags, s_out, ax_out, f_out);
     // the record, evaluated once in FP64 from the raw inputs and the crossed planes
     double sd, cd;
     sincos((double)phi, &sd, &cd);
@@ -93,6 +94,47 @@ k_prepare(GridC g, const uint8_t* __restrict__ mask, unsigned* flags, const floa
     rec[R_PY * stride + i] = (float)((fma(si, Di[1], Ti[1]) - (double)g.oy) / (double)g.dy);
     rec[R_PZ * stride + i] = (float)((fma(si, Di[2], Ti[2]) - (double)g.oz) / (double)g.dz);
     rec[R_B * stride + i] = wepl;
+}
+
+// Chessboard distance of every voxel to the nearest hull voxel, capped at 255
+// (the skipping table of the hull search), in three separable passes:
+//   f1(v) = min over hull voxels h of its x row      |v_x - h_x|
+//   f2(v) = min over y' of max(|v_y - y'|, f1(v_x, y', v_z))
+//   f3(v) = min over z' of max(|v_z - z'|, f2(v_x, v_y, z'))
+// which is min over hull voxels h of max(|v_x-h_x|, |v_y-h_y|, |v_z-h_z|).
+__global__ void k_hull_dist_x(const uint8_t* __restrict__ mask, int nx, int64_t rows,
+                              uint8_t* __restrict__ out)
+{
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const uint8_t* m = mask + r * nx;
+    uint8_t* o = out + r * nx;
+    int last = -1;
+    for (int x = 0; x < nx; ++x) {
+        if (m[x]) last = x;
+        o[x] = (uint8_t)(last < 0 ? 255 : min(x - last, 255));
+    }
+    last = -1;
+    for (int x = nx - 1; x >= 0; --x) {
+        if (m[x]) last = x;
+        if (last >= 0) o[x] = (uint8_t)min((int)o[x], min(last - x, 255));
+    }
+}
+
+// One of the min-max passes along an axis of n voxels with element stride
+// `stride` (f2 from f1 along y, f3 from f2 along z).
+__global__ void k_hull_dist_axis(const uint8_t* __restrict__ in, int n, int64_t stride, int64_t n_vox,
+                                 uint8_t* __restrict__ out)
+{
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= n_vox) return;
+    const int a = (int)((v / stride) % n);
+    int best = in[v];
+    for (int r = 1; r < best; ++r) {
+        if (a - r >= 0) best = min(best, max(r, (int)in[v - r * stride]));
+        if (a + r < n) best = min(best, max(r, (int)in[v + r * stride]));
+    }
+    out[v] = (uint8_t)best;
 }
 
 __global__ void k_hull_states(const float* __restrict__ rec, int64_t stride, int64_t first,
@@ -147,7 +189,7 @@ k_mlp_points(GridC g, MlpC mc, RecView rv, int64_t first, int64_t count, int32_t
 constexpr int kRunSlots = 24;
 // warp-per-proton kernels: at most 256 threads per CTA, 64 registers per thread
 constexpr int kWarpCta = 256;
-constexpr int kWarpCtaMin = 4;
+constexpr int kWarpCtaMin = 3;
 constexpr int kRowSlots = 64;
 
 __device__ __forceinline__ RunSlots warp_slots(unsigned char* smem, int rl)
@@ -247,24 +289,26 @@ k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsign
 // DROP block step (a3-a6 fused), one warp per proton of the block, x frozen:
 //   r_i = (b_i - a_i.x) / ||a_i||^2, then acc[j] += (a_ij r_i, 1) over its row.
 // The row is walked once; the scatter replays the runs kept in shared memory.
+// The grid fills the GPU once and each warp strides over the block's protons.
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
              int64_t first, int64_t count, const float* __restrict__ x, float2* acc)
 {
     extern __shared__ unsigned char smem[];
-    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (t >= count) return;
+    const RunSlots slots = warp_slots(smem, kRunSlots);
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < count; t += nw) {
     const int64_t i = first + t;
     Path P;
-    if (!load_path(rv, i, mc, P)) return;
-    const RunSlots slots = warp_slots(smem, kRunSlots);
+    if (!load_path(rv, i, mc, P)) continue;
     LaneWalk w;
     float s, q;
     warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
-    if (!(q > 0.f)) return;
+    if (!(q > 0.f)) continue;
     const float r = (rv.get(R_B, i) - s) / q;
     replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
                            [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
+    }
 }
 
 // DROP block apply (a7): x_j += lambda * num_j / s_j where the block touched
@@ -298,9 +342,23 @@ cudaError_t launch_prepare(const Launch& L, const Geo& G, const float* hist, int
                              (float)G.g.ny * G.g.dy * (float)G.g.ny * G.g.dy +
                              (float)G.g.nz * G.g.dz * (float)G.g.nz * G.g.dz);
     const float Lmax = fminf(diag * 1.0001f + 1e-3f, (float)(G.mc.kmax - 2) * G.mc.du_mm);
-    k_prepare<<<grid_for(n, L.cta), L.cta, 0, L.stream>>>(G.g, G.mask, G.flags, hist, stride, 0, n,
-                                                          rec, Lmax);
+    k_prepare<<<grid_for(n, L.cta), L.cta, 0, L.stream>>>(G.g, G.mask, G.dist, G.flags, hist, stride, 0,
+                                                          n, rec, Lmax);
     PCT_LAUNCH_TAIL(L);
+}
+
+cudaError_t launch_hull_dist(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, uint8_t* tmp,
+                             uint8_t* dist)
+{
+    const int64_t n_vox = (int64_t)nx * ny * nz;
+    if (n_vox <= 0) return cudaSuccess;
+    const int64_t rows = (int64_t)ny * nz;
+    k_hull_dist_x<<<(unsigned)((rows + 255) / 256), 256, 0, L.stream>>>(mask, nx, rows, dist);
+    const unsigned blocks = (unsigned)((n_vox + 255) / 256);
+    k_hull_dist_axis<<<blocks, 256, 0, L.stream>>>(dist, ny, nx, n_vox, tmp);
+    k_hull_dist_axis<<<blocks, 256, 0, L.stream>>>(tmp, nz, (int64_t)nx * ny, n_vox, dist);
+    *L.launches += 3;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_hull_states(const Launch& L, const float* rec, int64_t stride, int64_t first,
@@ -382,7 +440,24 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
     const size_t sm = slot_bytes(L.cta, kRunSlots);
     cudaError_t e = allow_smem(k_drop_fused, sm);
     if (e != cudaSuccess) return e;
-    k_drop_fused<<<warp_grid(count, L.cta), L.cta, sm, L.stream>>>(
+    unsigned grid = warp_grid(count, L.cta);
+    // fill the GPU exactly once (resident CTAs per SM x SMs); warps stride
+    // over the block's protons, so no partial wave is left at the tail
+    thread_local int fill_dev = -1, fill_cta = -1, fill = 0;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (fill_dev != dev || fill_cta != L.cta) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_drop_fused, L.cta, sm);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        fill = per_sm * sms;
+        fill_dev = dev;
+        fill_cta = L.cta;
+    }
+    if (fill > 0 && grid > (unsigned)fill) grid = (unsigned)fill;
+    k_drop_fused<<<grid, L.cta, sm, L.stream>>>(
         G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, first, count, x, acc);
     PCT_LAUNCH_TAIL(L);
 }

@@ -23,6 +23,8 @@ static __device__ __align__(256) float g_rec[R_NF * PCT_NOALLOC_MAX_PROTONS];
 static __device__ __align__(256) float2 g_acc[PCT_NOALLOC_MAX_VOXELS];
 static __device__ __align__(256) float4 g_sig1[PCT_NOALLOC_MAX_SAMPLES + 1];
 static __device__ __align__(256) unsigned g_flags[1];
+static __device__ __align__(256) uint8_t g_dist[PCT_NOALLOC_MAX_VOXELS];
+static __device__ __align__(256) uint8_t g_dist_tmp[PCT_NOALLOC_MAX_VOXELS];
 
 struct Scratch {
     bool ready = false;
@@ -31,6 +33,8 @@ struct Scratch {
     float2* acc = nullptr;
     float4* sig1 = nullptr;
     unsigned* flags = nullptr;
+    uint8_t* dist = nullptr;
+    uint8_t* dist_tmp = nullptr;
 };
 
 Scratch g_scratch[kMaxDevices];
@@ -67,7 +71,9 @@ pct_status scratch_for(int device, Scratch& out)
             (e = cudaGetSymbolAddress((void**)&s.rec, g_rec)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&s.acc, g_acc)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&s.sig1, g_sig1)) != cudaSuccess ||
-            (e = cudaGetSymbolAddress((void**)&s.flags, g_flags)) != cudaSuccess)
+            (e = cudaGetSymbolAddress((void**)&s.flags, g_flags)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&s.dist, g_dist)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&s.dist_tmp, g_dist_tmp)) != cudaSuccess)
             return cuda_fail(e, "scratch address lookup");
         s.ready = true;
     }
@@ -188,6 +194,7 @@ extern "C" pct_status pct_solve_noalloc(const pct_grid* grid, const uint8_t* hul
     const double vdiag = std::sqrt((double)G.dx * G.dx + (double)G.dy * G.dy + (double)G.dz * G.dz);
     geo.mc.cmin = (int)std::floor(vdiag / du) + 1;
     geo.mask = hull_mask;
+    geo.dist = S.dist;
     geo.flags = S.flags;
     int64_t launches = 0;
     const Launch L{stream, 256, &launches};
@@ -199,6 +206,8 @@ extern "C" pct_status pct_solve_noalloc(const pct_grid* grid, const uint8_t* hul
                                 cudaMemcpyDeviceToDevice, stream);
             if (e != cudaSuccess) return cuda_fail(e, "history copy");
         }
+        if ((e = launch_hull_dist(L, hull_mask, G.nx, G.ny, G.nz, S.dist_tmp, S.dist)) != cudaSuccess)
+            return cuda_fail(e, "hull distance map");
         if ((e = launch_prepare(L, geo, S.hist, stride, n, S.rec)) != cudaSuccess)
             return cuda_fail(e, "prepare kernel");
         // the accumulator must start at zero; every block apply leaves it at zero

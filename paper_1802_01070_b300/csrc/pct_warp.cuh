@@ -97,9 +97,10 @@ __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const
         }
         const float Dx = bx - ax, Dy = by - ay, Dz = bz - az;
         const float ex = Dx * g.dx, ey = Dy * g.dy, ez = Dz * g.dz;
-        const float len = __fsqrt_rn(fmaf(ex, ex, fmaf(ey, ey, ez * ez)));
+        const float l2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+        const float len = l2 > 0.f ? l2 * rsqrtf(l2) : 0.f;
         const int sx = Dx > 0.f ? 1 : -1, sy = Dy > 0.f ? 1 : -1, sz = Dz > 0.f ? 1 : -1;
-        const float rx = __frcp_rn(Dx), ry = __frcp_rn(Dy), rz = __frcp_rn(Dz);
+        const float rx = __fdividef(1.f, Dx), ry = __fdividef(1.f, Dy), rz = __fdividef(1.f, Dz);
         float tmx = Dx > 0.f ? (float)(ix + 1) - ax : (Dx < 0.f ? (float)ix - ax : INF);
         float tmy = Dy > 0.f ? (float)(iy + 1) - ay : (Dy < 0.f ? (float)iy - ay : INF);
         float tmz = Dz > 0.f ? (float)(iz + 1) - az : (Dz < 0.f ? (float)iz - az : INF);
