@@ -294,9 +294,10 @@ pct_status pct_reset_stats(pct_ctx *ctx);
  * kernels, MLP spacing = smallest voxel edge), but takes every input as a
  * device pointer and keeps all scratch (a copy of the histories, the
  * per-proton records, the per-voxel DROP accumulator, the hull distance map
- * of the hull search and its scratch, the MLP table) in fixed device arrays
- * compiled into the library: about 18 MB, held on every GPU that loads the
- * library until the process exits.  Limits: at most
+ * of the hull search and its scratch, the per-block lists of protons with a
+ * hull path, the MLP table) in fixed device arrays compiled into the library:
+ * about 19 MB, held on every GPU that loads the library until the process
+ * exits.  Limits: at most
  * PCT_NOALLOC_MAX_PROTONS protons, PCT_NOALLOC_MAX_VOXELS voxels, and a grid
  * diagonal of at most PCT_NOALLOC_MAX_SAMPLES MLP steps; larger inputs are
  * rejected with PCT_ERR_ARG before any GPU work.

@@ -44,6 +44,11 @@ struct pct_ctx {
     float* d_hist = nullptr;
     float* d_rec = nullptr;
     float2* d_acc = nullptr;
+    // lists of the protons with a hull path per DROP block (fused solve)
+    int64_t* d_vidx = nullptr;
+    int64_t* d_boff = nullptr;
+    int64_t* d_chunk = nullptr;
+    int64_t vidx_cap = 0, boff_cap = 0, chunk_cap = 0;
     float* d_xtmp = nullptr;
     // stored rows (PCT_MODE_CSR / PCT_MODE_PACKED)
     int mode = PCT_MODE_FUSED;
@@ -237,6 +242,32 @@ pct_status ensure_acc(pct_ctx* c)
     if (s != PCT_OK) return s;
     c->d_acc = (float2*)p;
     return PCT_OK;
+}
+
+pct_status ensure_i64(pct_ctx* c, int64_t** p, int64_t* cap, int64_t need, const char* what)
+{
+    if (*p && *cap >= need) return PCT_OK;
+    dfree(c, *p);
+    *p = nullptr;
+    *cap = 0;
+    void* q = nullptr;
+    pct_status s = dalloc(c, &q, (size_t)need * sizeof(int64_t), what);
+    if (s != PCT_OK) return s;
+    *p = (int64_t*)q;
+    *cap = need;
+    return PCT_OK;
+}
+
+// Valid-proton lists of the DROP blocks of size B (after prepare).
+pct_status compact(pct_ctx* c, int64_t B)
+{
+    pct_status s;
+    if ((s = ensure_i64(c, &c->d_vidx, &c->vidx_cap, c->n, "valid-proton list")) != PCT_OK ||
+        (s = ensure_i64(c, &c->d_boff, &c->boff_cap, (c->n + B - 1) / B + 1, "block offsets")) != PCT_OK ||
+        (s = ensure_i64(c, &c->d_chunk, &c->chunk_cap, compact_chunks(c->n), "compaction scratch")) != PCT_OK)
+        return s;
+    cudaError_t e = launch_compact(launch_of(c), c->d_rec, c->stride, c->n, B, c->d_chunk, c->d_vidx, c->d_boff);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "valid-proton lists");
 }
 
 int64_t row_bytes(const pct_ctx* c)
@@ -699,6 +730,7 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
     if ((s = ensure_acc(c)) != PCT_OK) return s;
     if (c->mode == PCT_MODE_FUSED) {
         if ((s = prepare(c)) != PCT_OK) return s;
+        if ((s = compact(c, block_size)) != PCT_OK) return s;
     } else if (c->rows_mode != c->mode) {
         if ((s = build_rows(c)) != PCT_OK) return s;
     }
@@ -722,7 +754,8 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
                 e = launch_drop_packed(L, c->gc, c->d_flags, c->d_rowptr, c->d_start, c->d_codes, c->d_lens16, b,
                                        first, count, x, c->d_acc);
             else
-                e = launch_drop_fused(L, G, c->d_rec, c->stride, first, count, x, c->d_acc);
+                e = launch_drop_fused(L, G, c->d_rec, c->stride, c->d_vidx, c->d_boff, first / block_size,
+                                      count, x, c->d_acc);
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP kernel");
             ++c->fused_launches;
             if (e1) cudaEventRecord(e1, c->stream);

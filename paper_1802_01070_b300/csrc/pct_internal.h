@@ -46,8 +46,18 @@ cudaError_t launch_forward(const Launch& L, const Geo& G, const float* rec, int6
                            int64_t n, const float* x, float* y);
 cudaError_t launch_adjoint(const Launch& L, const Geo& G, const float* rec, int64_t stride,
                            int64_t n, const float* y, float* g_out);
+// Lists of the protons whose path crosses the hull, per DROP block of size B:
+// block k's protons are vidx[boff[k] .. boff[k+1]) (proton order).  chunk is
+// scratch of compact_chunks(n) values; vidx holds n values, boff
+// ceil(n / B) + 1.
+constexpr int64_t kCompactChunk = 8192;   // protons per compaction chunk
+int64_t compact_chunks(int64_t n);
+cudaError_t launch_compact(const Launch& L, const float* rec, int64_t stride, int64_t n, int64_t B,
+                           int64_t* chunk, int64_t* vidx, int64_t* boff);
+// DROP block step of block k (at most `count` protons) over its valid list.
 cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                              int64_t first, int64_t count, const float* x, float2* acc);
+                              const int64_t* vidx, const int64_t* boff, int64_t k, int64_t count,
+                              const float* x, float2* acc);
 cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda);
 
 // gradient-based reconstruction (pct_grad.cu)

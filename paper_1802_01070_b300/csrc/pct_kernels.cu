@@ -290,24 +290,29 @@ k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsign
 //   r_i = (b_i - a_i.x) / ||a_i||^2, then acc[j] += (a_ij r_i, 1) over its row.
 // The row is walked once; the scatter replays the runs kept in shared memory.
 // The grid fills the GPU once and each warp strides over the block's protons.
+// The block's protons are the entries vidx[boff[k] .. boff[k+1]) of the list
+// of protons whose path crosses the hull (the others have empty rows), so no
+// warp is spent on a proton without work.
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
-             int64_t first, int64_t count, const float* __restrict__ x, float2* acc)
+             const int64_t* __restrict__ vidx, const int64_t* __restrict__ boff, int64_t k,
+             const float* __restrict__ x, float2* acc)
 {
     extern __shared__ unsigned char smem[];
     const RunSlots slots = warp_slots(smem, kRunSlots);
+    const int64_t lo = boff[k], count = boff[k + 1] - lo;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < count; t += nw) {
-    const int64_t i = first + t;
-    Path P;
-    if (!load_path(rv, i, mc, P)) continue;
-    LaneWalk w;
-    float s, q;
-    warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
-    if (!(q > 0.f)) continue;
-    const float r = (rv.get(R_B, i) - s) / q;
-    replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
-                           [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
+        const int64_t i = vidx[lo + t];
+        Path P;
+        if (!load_path(rv, i, mc, P)) continue;
+        LaneWalk w;
+        float s, q;
+        warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
+        if (!(q > 0.f)) continue;
+        const float r = (rv.get(R_B, i) - s) / q;
+        replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
+                               [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
     }
 }
 
@@ -434,11 +439,13 @@ cudaError_t launch_adjoint(const Launch& L, const Geo& G, const float* rec, int6
 }
 
 cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                              int64_t first, int64_t count, const float* x, float2* acc)
+                              const int64_t* vidx, const int64_t* boff, int64_t k, int64_t count,
+                              const float* x, float2* acc)
 {
     if (count <= 0) return cudaSuccess;
     const size_t sm = slot_bytes(L.cta, kRunSlots);
-    cudaError_t e = allow_smem(k_drop_fused, sm);
+    auto kernel = k_drop_fused;
+    cudaError_t e = allow_smem(kernel, sm);
     if (e != cudaSuccess) return e;
     unsigned grid = warp_grid(count, L.cta);
     // fill the GPU exactly once (resident CTAs per SM x SMs); warps stride
@@ -449,7 +456,7 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
     if (e != cudaSuccess) return e;
     if (fill_dev != dev || fill_cta != L.cta) {
         int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_drop_fused, L.cta, sm);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, L.cta, sm);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         fill = per_sm * sms;
@@ -457,9 +464,116 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
         fill_cta = L.cta;
     }
     if (fill > 0 && grid > (unsigned)fill) grid = (unsigned)fill;
-    k_drop_fused<<<grid, L.cta, sm, L.stream>>>(
-        G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, first, count, x, acc);
+    kernel<<<grid, L.cta, sm, L.stream>>>(
+        G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff, k, x, acc);
     PCT_LAUNCH_TAIL(L);
+}
+
+// ---------------------------------------------------------------------------
+// Valid-proton lists of the DROP blocks.  Three passes over the records:
+// count the protons with a hull path (L > 0) per chunk, scan the chunk counts,
+// and write each valid proton's index at its exclusive prefix (so the list
+// keeps proton order and every block's protons stay together); the prefix at
+// each block start is the block's offset in the list.
+// ---------------------------------------------------------------------------
+constexpr int kCompactCta = 256;
+constexpr int kCompactRounds = (int)(kCompactChunk / kCompactCta);
+static_assert(kCompactChunk % kCompactCta == 0, "compaction chunk must be whole CTA rounds");
+constexpr int kCompactScanCta = 1024;
+
+__device__ __forceinline__ bool has_path(const float* __restrict__ rec, int64_t stride, int64_t n, int64_t i)
+{
+    return i < n && rec[R_L * stride + i] > 0.f;
+}
+
+__global__ void __launch_bounds__(kCompactCta)
+k_compact_count(const float* __restrict__ rec, int64_t stride, int64_t n, int64_t* __restrict__ chunk_count)
+{
+    __shared__ int part[kCompactCta / 32];
+    const int64_t base = blockIdx.x * kCompactChunk;
+    int c = 0;
+    for (int r = 0; r < kCompactRounds; ++r) c += has_path(rec, stride, n, base + r * kCompactCta + threadIdx.x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t t = 0;
+        for (int w = 0; w < kCompactCta / 32; ++w) t += part[w];
+        chunk_count[blockIdx.x] = t;
+    }
+}
+
+// One CTA: exclusive scan of the chunk counts in place; the total goes to
+// boff[nblocks].
+__global__ void __launch_bounds__(kCompactScanCta)
+k_compact_scan(int64_t* __restrict__ chunk, int64_t nchunks, int64_t* __restrict__ boff, int64_t nblocks)
+{
+    __shared__ int64_t part[kCompactScanCta];
+    const int64_t per = (nchunks + kCompactScanCta - 1) / kCompactScanCta;
+    const int64_t a = threadIdx.x * per, b = a + per < nchunks ? a + per : nchunks;
+    int64_t sum = 0;
+    for (int64_t c = a; c < b; ++c) sum += chunk[c];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the per-thread sums
+    for (int o = 1; o < kCompactScanCta; o <<= 1) {
+        const int64_t v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = part[threadIdx.x] - sum;
+    for (int64_t c = a; c < b; ++c) {
+        const int64_t v = chunk[c];
+        chunk[c] = run;
+        run += v;
+    }
+    if (threadIdx.x == kCompactScanCta - 1) boff[nblocks] = part[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kCompactCta)
+k_compact_fill(const float* __restrict__ rec, int64_t stride, int64_t n, int64_t B,
+               const int64_t* __restrict__ chunk_off, int64_t* __restrict__ vidx, int64_t* __restrict__ boff)
+{
+    __shared__ int part[kCompactCta / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t base = blockIdx.x * kCompactChunk;
+    int64_t run = chunk_off[blockIdx.x];
+    for (int r = 0; r < kCompactRounds; ++r) {
+        const int64_t i = base + r * kCompactCta + threadIdx.x;
+        const bool v = has_path(rec, stride, n, i);
+        const unsigned bal = __ballot_sync(0xffffffffu, v);
+        if (lane == 0) part[warp] = __popc(bal);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < kCompactCta / 32; ++w) {
+            before += w < warp ? part[w] : 0;
+            total += part[w];
+        }
+        const int64_t pos = run + before + __popc(bal & ((1u << lane) - 1u));
+        if (i < n && i % B == 0) boff[i / B] = pos;
+        if (v) vidx[pos] = i;
+        run += total;
+        __syncthreads();
+    }
+}
+
+int64_t compact_chunks(int64_t n)
+{
+    return (n + kCompactChunk - 1) / kCompactChunk;
+}
+
+cudaError_t launch_compact(const Launch& L, const float* rec, int64_t stride, int64_t n, int64_t B,
+                           int64_t* chunk, int64_t* vidx, int64_t* boff)
+{
+    if (n <= 0 || B <= 0) return cudaSuccess;
+    const int64_t nc = compact_chunks(n), nblocks = (n + B - 1) / B;
+    k_compact_count<<<(unsigned)nc, kCompactCta, 0, L.stream>>>(rec, stride, n, chunk);
+    k_compact_scan<<<1, kCompactScanCta, 0, L.stream>>>(chunk, nc, boff, nblocks);
+    k_compact_fill<<<(unsigned)nc, kCompactCta, 0, L.stream>>>(rec, stride, n, B, chunk, vidx, boff);
+    *L.launches += 3;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda)

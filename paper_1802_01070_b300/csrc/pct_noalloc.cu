@@ -23,6 +23,9 @@ static __device__ __align__(256) float g_rec[R_NF * PCT_NOALLOC_MAX_PROTONS];
 static __device__ __align__(256) float2 g_acc[PCT_NOALLOC_MAX_VOXELS];
 static __device__ __align__(256) float4 g_sig1[PCT_NOALLOC_MAX_SAMPLES + 1];
 static __device__ __align__(256) unsigned g_flags[1];
+static __device__ __align__(256) int64_t g_vidx[PCT_NOALLOC_MAX_PROTONS];
+static __device__ __align__(256) int64_t g_boff[PCT_NOALLOC_MAX_PROTONS + 1];
+static __device__ __align__(256) int64_t g_chunk[PCT_NOALLOC_MAX_PROTONS / kCompactChunk + 1];
 static __device__ __align__(256) uint8_t g_dist[PCT_NOALLOC_MAX_VOXELS];
 static __device__ __align__(256) uint8_t g_dist_tmp[PCT_NOALLOC_MAX_VOXELS];
 
@@ -35,6 +38,9 @@ struct Scratch {
     unsigned* flags = nullptr;
     uint8_t* dist = nullptr;
     uint8_t* dist_tmp = nullptr;
+    int64_t* vidx = nullptr;
+    int64_t* boff = nullptr;
+    int64_t* chunk = nullptr;
 };
 
 Scratch g_scratch[kMaxDevices];
@@ -73,7 +79,10 @@ pct_status scratch_for(int device, Scratch& out)
             (e = cudaGetSymbolAddress((void**)&s.sig1, g_sig1)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&s.flags, g_flags)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&s.dist, g_dist)) != cudaSuccess ||
-            (e = cudaGetSymbolAddress((void**)&s.dist_tmp, g_dist_tmp)) != cudaSuccess)
+            (e = cudaGetSymbolAddress((void**)&s.dist_tmp, g_dist_tmp)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&s.vidx, g_vidx)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&s.boff, g_boff)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&s.chunk, g_chunk)) != cudaSuccess)
             return cuda_fail(e, "scratch address lookup");
         s.ready = true;
     }
@@ -210,13 +219,16 @@ extern "C" pct_status pct_solve_noalloc(const pct_grid* grid, const uint8_t* hul
             return cuda_fail(e, "hull distance map");
         if ((e = launch_prepare(L, geo, S.hist, stride, n, S.rec)) != cudaSuccess)
             return cuda_fail(e, "prepare kernel");
+        if ((e = launch_compact(L, S.rec, stride, n, block_size, S.chunk, S.vidx, S.boff)) != cudaSuccess)
+            return cuda_fail(e, "valid-proton lists");
         // the accumulator must start at zero; every block apply leaves it at zero
         if ((e = cudaMemsetAsync(S.acc, 0, (size_t)n_vox * sizeof(float2), stream)) != cudaSuccess)
             return cuda_fail(e, "accumulator clear");
         for (int32_t it = 0; it < iters; ++it) {
             for (int64_t first = 0; first < n; first += block_size) {
                 const int64_t count = block_size < n - first ? block_size : n - first;
-                if ((e = launch_drop_fused(L, geo, S.rec, stride, first, count, x, S.acc)) != cudaSuccess)
+                if ((e = launch_drop_fused(L, geo, S.rec, stride, S.vidx, S.boff, first / block_size, count, x,
+                                           S.acc)) != cudaSuccess)
                     return cuda_fail(e, "DROP kernel");
                 if ((e = launch_drop_apply(L, n_vox, x, S.acc, lambda)) != cudaSuccess)
                     return cuda_fail(e, "DROP apply kernel");
