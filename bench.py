@@ -169,6 +169,26 @@ def _measured_peaks():
 
 
 # ----------------------------------------------------------------------------
+# Multi-rank aggregation: every rank runs an independent replica of the scan
+# (the solve does not shard), the job's time is its slowest rank's
+# ----------------------------------------------------------------------------
+
+def max_over_ranks(value, dist=None):
+    """Largest `value` over all ranks of the process group (itself at N = 1)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput of `world` replicas that each process `units_per_rank`."""
+    return world * units_per_rank / seconds
+
+
+# ----------------------------------------------------------------------------
 # CPU oracle leg (test infrastructure; timed as it stands)
 # ----------------------------------------------------------------------------
 
@@ -327,11 +347,8 @@ def run_ours(args):
     fused_n = int(ctx.stat(pct.PCT_STAT_FUSED_LAUNCHES))
     ctx.set_option(pct.PCT_OPT_TIMING, 0)
     ctx.reset_stats()
-    if dist:
-        t = torch.tensor([step_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = world * valid * cfg.iters / (step_ms * 1e-3)
+    step_ms = max_over_ranks(step_ms, dist)
+    value = replica_throughput(world, valid * cfg.iters, step_ms * 1e-3)
 
     # roofline of the dominant kernel (fused DROP block step)
     peaks = _measured_peaks()
@@ -397,12 +414,8 @@ def run_ours(args):
             ctx.load_histories(host)
             ctx.solve_host(xw.numpy(), cfg.iters, cfg.lam, block)
             times.append(time.perf_counter() - t0)
-        te = statistics.mean(times[1:])
-        if dist:
-            t = torch.tensor([te], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
-        out["e2e"] = {"value": world * valid * cfg.iters / te, "unit": UNIT,
+        te = max_over_ranks(statistics.mean(times[1:]), dist)
+        out["e2e"] = {"value": replica_throughput(world, valid * cfg.iters, te), "unit": UNIT,
                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": xh.numel() * 4,
                       "recon_s": te}
     else:
