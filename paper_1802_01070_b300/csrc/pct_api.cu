@@ -39,6 +39,7 @@ struct pct_ctx {
     int kmax = 0;
     int64_t du_um = 0;
     unsigned* d_flags = nullptr;
+    unsigned long long* d_next = nullptr;   // work counter of the fused block step
     bool loaded = false;                 // pct_load_histories has succeeded once
     int64_t n = 0, stride = 0, cap = 0;  // protons, column stride, column capacity
     float* d_hist = nullptr;
@@ -480,6 +481,8 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const uint8_t* hull_m
         e = cudaMemset(c->d_flags, 0, sizeof(unsigned));
         if (e != cudaSuccess) s = cuda_fail(c, e, "flags");
     }
+    if (s == PCT_OK && (s = dalloc(c, &p, sizeof(unsigned long long), "work counter")) == PCT_OK)
+        c->d_next = (unsigned long long*)p;
     if (s == PCT_OK) s = build_sigma_table(c);
     if (s != PCT_OK) {
         g_create_error = "pct_create: " + c->err;
@@ -735,6 +738,7 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
         if ((s = build_rows(c)) != PCT_OK) return s;
     }
     cudaError_t e = cudaMemsetAsync(c->d_acc, 0, (size_t)c->n_vox * sizeof(float2), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_next, 0, sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "accumulator clear");
     const Launch L = launch_of(c);
     const Geo G = geo_of(c);
@@ -755,11 +759,11 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
                                        first, count, x, c->d_acc);
             else
                 e = launch_drop_fused(L, G, c->d_rec, c->stride, c->d_vidx, c->d_boff, first / block_size,
-                                      count, x, c->d_acc);
+                                      count, x, c->d_acc, c->d_next);
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP kernel");
             ++c->fused_launches;
             if (e1) cudaEventRecord(e1, c->stream);
-            e = launch_drop_apply(L, c->n_vox, x, c->d_acc, lambda);
+            e = launch_drop_apply(L, c->n_vox, x, c->d_acc, lambda, c->d_next);
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP apply kernel");
         }
     }

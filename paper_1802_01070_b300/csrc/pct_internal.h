@@ -54,11 +54,15 @@ constexpr int64_t kCompactChunk = 8192;   // protons per compaction chunk
 int64_t compact_chunks(int64_t n);
 cudaError_t launch_compact(const Launch& L, const float* rec, int64_t stride, int64_t n, int64_t B,
                            int64_t* chunk, int64_t* vidx, int64_t* boff);
-// DROP block step of block k (at most `count` protons) over its valid list.
+// DROP block step of block k (at most `count` protons) over its valid list;
+// `next` is a device work counter that must be zero at launch (the block
+// apply that follows resets it).
 cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, int64_t stride,
                               const int64_t* vidx, const int64_t* boff, int64_t k, int64_t count,
-                              const float* x, float2* acc);
-cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda);
+                              const float* x, float2* acc, unsigned long long* next);
+// Block apply; resets the work counter `next` when not null.
+cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda,
+                              unsigned long long* next);
 
 // gradient-based reconstruction (pct_grad.cu)
 cudaError_t launch_tv(const Launch& L, const float* x, int nx, int ny, int nz, float eps, float* grad,

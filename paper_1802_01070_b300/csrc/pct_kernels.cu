@@ -289,38 +289,53 @@ k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsign
 // DROP block step (a3-a6 fused), one warp per proton of the block, x frozen:
 //   r_i = (b_i - a_i.x) / ||a_i||^2, then acc[j] += (a_ij r_i, 1) over its row.
 // The row is walked once; the scatter replays the runs kept in shared memory.
-// The grid fills the GPU once and each warp strides over the block's protons.
 // The block's protons are the entries vidx[boff[k] .. boff[k+1]) of the list
-// of protons whose path crosses the hull (the others have empty rows), so no
-// warp is spent on a proton without work.
+// of protons whose path crosses the hull (the others have empty rows).  The
+// grid fills the GPU once; each warp takes a first chunk of kGrab protons by
+// its index and further chunks from the counter *next (zero at launch), so
+// that warps whose paths were short take more of them and the launch ends
+// evenly.
+constexpr int kGrab = 4;
+
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
              const int64_t* __restrict__ vidx, const int64_t* __restrict__ boff, int64_t k,
-             const float* __restrict__ x, float2* acc)
+             const float* __restrict__ x, float2* acc, unsigned long long* next)
 {
     extern __shared__ unsigned char smem[];
     const RunSlots slots = warp_slots(smem, kRunSlots);
     const int64_t lo = boff[k], count = boff[k + 1] - lo;
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); t < count; t += nw) {
-        const int64_t i = vidx[lo + t];
-        Path P;
-        if (!load_path(rv, i, mc, P)) continue;
-        LaneWalk w;
-        float s, q;
-        warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
-        if (!(q > 0.f)) continue;
-        const float r = (rv.get(R_B, i) - s) / q;
-        replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
-                               [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
+    const int lane = threadIdx.x & (kWarp - 1);
+    int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * kGrab;
+    while (base < count) {
+        const int64_t end = base + kGrab < count ? base + kGrab : count;
+        for (int64_t t = base; t < end; ++t) {
+            const int64_t i = vidx[lo + t];
+            Path P;
+            if (!load_path(rv, i, mc, P)) continue;
+            LaneWalk w;
+            float s, q;
+            warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
+            if (!(q > 0.f)) continue;
+            const float r = (rv.get(R_B, i) - s) / q;
+            replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
+                                   [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
+        }
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(next, (unsigned long long)kGrab);
+        base = nw * kGrab + (int64_t)__shfl_sync(0xffffffffu, got, 0);
     }
 }
 
 // DROP block apply (a7): x_j += lambda * num_j / s_j where the block touched
 // voxel j, and clear the accumulator for the next block.
+// `next` (if not null): the work counter of the block step, reset here for
+// the next block step on the stream.
 __global__ void k_drop_apply(int64_t n_vox, float* __restrict__ x, float2* __restrict__ acc,
-                             float lambda)
+                             float lambda, unsigned long long* next)
 {
+    if (next && blockIdx.x == 0 && threadIdx.x == 0) *next = 0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_vox; j += stride) {
         const float2 a = acc[j];
@@ -440,14 +455,14 @@ cudaError_t launch_adjoint(const Launch& L, const Geo& G, const float* rec, int6
 
 cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, int64_t stride,
                               const int64_t* vidx, const int64_t* boff, int64_t k, int64_t count,
-                              const float* x, float2* acc)
+                              const float* x, float2* acc, unsigned long long* next)
 {
     if (count <= 0) return cudaSuccess;
     const size_t sm = slot_bytes(L.cta, kRunSlots);
     auto kernel = k_drop_fused;
     cudaError_t e = allow_smem(kernel, sm);
     if (e != cudaSuccess) return e;
-    unsigned grid = warp_grid(count, L.cta);
+    unsigned grid = warp_grid((count + kGrab - 1) / kGrab, L.cta);
     // fill the GPU exactly once (resident CTAs per SM x SMs); warps stride
     // over the block's protons, so no partial wave is left at the tail
     thread_local int fill_dev = -1, fill_cta = -1, fill = 0;
@@ -465,7 +480,7 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
     }
     if (fill > 0 && grid > (unsigned)fill) grid = (unsigned)fill;
     kernel<<<grid, L.cta, sm, L.stream>>>(
-        G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff, k, x, acc);
+        G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff, k, x, acc, next);
     PCT_LAUNCH_TAIL(L);
 }
 
@@ -576,12 +591,13 @@ cudaError_t launch_compact(const Launch& L, const float* rec, int64_t stride, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda)
+cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda,
+                              unsigned long long* next)
 {
     if (n_vox <= 0) return cudaSuccess;
     int64_t blocks = (n_vox + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
-    k_drop_apply<<<(unsigned)blocks, 256, 0, L.stream>>>(n_vox, x, acc, lambda);
+    k_drop_apply<<<(unsigned)blocks, 256, 0, L.stream>>>(n_vox, x, acc, lambda, next);
     PCT_LAUNCH_TAIL(L);
 }
 

@@ -23,6 +23,7 @@ static __device__ __align__(256) float g_rec[R_NF * PCT_NOALLOC_MAX_PROTONS];
 static __device__ __align__(256) float2 g_acc[PCT_NOALLOC_MAX_VOXELS];
 static __device__ __align__(256) float4 g_sig1[PCT_NOALLOC_MAX_SAMPLES + 1];
 static __device__ __align__(256) unsigned g_flags[1];
+static __device__ __align__(256) unsigned long long g_next[1];
 static __device__ __align__(256) int64_t g_vidx[PCT_NOALLOC_MAX_PROTONS];
 static __device__ __align__(256) int64_t g_boff[PCT_NOALLOC_MAX_PROTONS + 1];
 static __device__ __align__(256) int64_t g_chunk[PCT_NOALLOC_MAX_PROTONS / kCompactChunk + 1];
@@ -41,6 +42,7 @@ struct Scratch {
     int64_t* vidx = nullptr;
     int64_t* boff = nullptr;
     int64_t* chunk = nullptr;
+    unsigned long long* next = nullptr;
 };
 
 Scratch g_scratch[kMaxDevices];
@@ -82,7 +84,8 @@ pct_status scratch_for(int device, Scratch& out)
             (e = cudaGetSymbolAddress((void**)&s.dist_tmp, g_dist_tmp)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&s.vidx, g_vidx)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&s.boff, g_boff)) != cudaSuccess ||
-            (e = cudaGetSymbolAddress((void**)&s.chunk, g_chunk)) != cudaSuccess)
+            (e = cudaGetSymbolAddress((void**)&s.chunk, g_chunk)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&s.next, g_next)) != cudaSuccess)
             return cuda_fail(e, "scratch address lookup");
         s.ready = true;
     }
@@ -221,16 +224,18 @@ extern "C" pct_status pct_solve_noalloc(const pct_grid* grid, const uint8_t* hul
             return cuda_fail(e, "prepare kernel");
         if ((e = launch_compact(L, S.rec, stride, n, block_size, S.chunk, S.vidx, S.boff)) != cudaSuccess)
             return cuda_fail(e, "valid-proton lists");
-        // the accumulator must start at zero; every block apply leaves it at zero
-        if ((e = cudaMemsetAsync(S.acc, 0, (size_t)n_vox * sizeof(float2), stream)) != cudaSuccess)
+        // the accumulator and the work counter must start at zero; every block
+        // apply leaves them at zero
+        if ((e = cudaMemsetAsync(S.acc, 0, (size_t)n_vox * sizeof(float2), stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(S.next, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
             return cuda_fail(e, "accumulator clear");
         for (int32_t it = 0; it < iters; ++it) {
             for (int64_t first = 0; first < n; first += block_size) {
                 const int64_t count = block_size < n - first ? block_size : n - first;
                 if ((e = launch_drop_fused(L, geo, S.rec, stride, S.vidx, S.boff, first / block_size, count, x,
-                                           S.acc)) != cudaSuccess)
+                                           S.acc, S.next)) != cudaSuccess)
                     return cuda_fail(e, "DROP kernel");
-                if ((e = launch_drop_apply(L, n_vox, x, S.acc, lambda)) != cudaSuccess)
+                if ((e = launch_drop_apply(L, n_vox, x, S.acc, lambda, S.next)) != cudaSuccess)
                     return cuda_fail(e, "DROP apply kernel");
             }
         }
