@@ -291,8 +291,10 @@ k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsign
 // The row is walked once; the scatter replays the runs kept in shared memory.
 // The block's protons are the entries vidx[boff[k] .. boff[k+1]) of the list
 // of protons whose path crosses the hull (the others have empty rows).  The
-// grid fills the GPU once; each warp takes a first chunk of kGrab protons by
-// its index and further chunks from the counter *next (zero at launch), so
+// grid has one warp per proton up to filling the GPU once.  Each warp takes a
+// first chunk of `first` protons by its index (first = 1 when the block is
+// smaller than kGrab warps' worth per warp, else kGrab) and, while protons are
+// left, chunks of kGrab protons from the counter *next (zero at launch), so
 // that warps whose paths were short take more of them and the launch ends
 // evenly.
 constexpr int kGrab = 4;
@@ -300,16 +302,17 @@ constexpr int kGrab = 4;
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
              const int64_t* __restrict__ vidx, const int64_t* __restrict__ boff, int64_t k,
-             const float* __restrict__ x, float2* acc, unsigned long long* next)
+             const float* __restrict__ x, float2* acc, unsigned long long* next, int first)
 {
     extern __shared__ unsigned char smem[];
     const RunSlots slots = warp_slots(smem, kRunSlots);
     const int64_t lo = boff[k], count = boff[k + 1] - lo;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t stat = (int64_t)gridDim.x * (blockDim.x >> 5) * first;   // protons assigned by index
     const int lane = threadIdx.x & (kWarp - 1);
-    int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * kGrab;
+    int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * first;
+    int64_t end = base + first;
     while (base < count) {
-        const int64_t end = base + kGrab < count ? base + kGrab : count;
+        end = end < count ? end : count;
         for (int64_t t = base; t < end; ++t) {
             const int64_t i = vidx[lo + t];
             Path P;
@@ -322,9 +325,11 @@ k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, uns
             replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
                                    [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
         }
+        if (stat >= count) break;   // the whole block was assigned by index
         unsigned long long got = 0;
         if (lane == 0) got = atomicAdd(next, (unsigned long long)kGrab);
-        base = nw * kGrab + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        base = stat + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        end = base + kGrab;
     }
 }
 
@@ -462,7 +467,7 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
     auto kernel = k_drop_fused;
     cudaError_t e = allow_smem(kernel, sm);
     if (e != cudaSuccess) return e;
-    unsigned grid = warp_grid((count + kGrab - 1) / kGrab, L.cta);
+    unsigned grid = warp_grid(count, L.cta);
     // fill the GPU exactly once (resident CTAs per SM x SMs); warps stride
     // over the block's protons, so no partial wave is left at the tail
     thread_local int fill_dev = -1, fill_cta = -1, fill = 0;
@@ -479,8 +484,10 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
         fill_cta = L.cta;
     }
     if (fill > 0 && grid > (unsigned)fill) grid = (unsigned)fill;
+    const int64_t warps = (int64_t)grid * (L.cta / kWarp);
+    const int first = count >= (int64_t)kGrab * warps ? kGrab : 1;
     kernel<<<grid, L.cta, sm, L.stream>>>(
-        G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff, k, x, acc, next);
+        G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff, k, x, acc, next, first);
     PCT_LAUNCH_TAIL(L);
 }
 
