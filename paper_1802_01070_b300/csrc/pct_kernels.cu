@@ -292,12 +292,12 @@ k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsign
 // The block's protons are the entries vidx[boff[k] .. boff[k+1]) of the list
 // of protons whose path crosses the hull (the others have empty rows).  The
 // grid has one warp per proton up to filling the GPU once.  Each warp takes a
-// first chunk of `first` protons by its index (first = 1 when the block is
-// smaller than kGrab warps' worth per warp, else kGrab) and, while protons are
+// first chunk of `first` protons by its index (kGrab when the block holds at
+// least kGrab protons per warp of the grid, else 1) and, while protons are
 // left, chunks of kGrab protons from the counter *next (zero at launch), so
 // that warps whose paths were short take more of them and the launch ends
 // evenly.
-constexpr int kGrab = 4;
+constexpr int kGrab = 2;
 
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
