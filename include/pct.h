@@ -72,8 +72,11 @@ enum pct_option {
     /* Device-memory cap in bytes for the context's own allocations; 0 = none.
      * An allocation that would pass it fails with PCT_ERR_OOM. */
     PCT_OPT_MEM_CAP_BYTES = 3,
-    /* 1: record CUDA events around each launch of the DROP block kernel so that
-     * pct_get_stat(PCT_STAT_FUSED_MS) reports its device time.  Default 0. */
+    /* k > 0: record CUDA events around every k-th launch of the DROP block
+     * kernel (1 = every launch) so that pct_get_stat(PCT_STAT_FUSED_MS) reports
+     * their summed device time and PCT_STAT_TIMED_LAUNCHES their number.  A
+     * timed launch costs the stream a few microseconds (the event records), so
+     * a long solve of small blocks is best sampled.  Default 0 (off). */
     PCT_OPT_TIMING = 4,
     /* How pct_solve gets the rows of A (one of enum pct_mode).  Default
      * PCT_MODE_FUSED.  Changing it drops stored rows. */
@@ -112,8 +115,8 @@ enum pct_mode {
 enum pct_stat {
     PCT_STAT_LAUNCHES = 1,        /* kernels launched by the library */
     PCT_STAT_FUSED_LAUNCHES = 2,  /* launches of the fused DROP kernel */
-    PCT_STAT_FUSED_MS = 3,        /* their summed device time, ms (needs PCT_OPT_TIMING;
-                                     synchronizes the stream) */
+    PCT_STAT_FUSED_MS = 3,        /* summed device time of the timed ones, ms (needs
+                                     PCT_OPT_TIMING; synchronizes the stream) */
     PCT_STAT_DEVICE_BYTES = 4,    /* device memory held by the context */
     PCT_STAT_N_PROTONS = 5,       /* protons loaded */
     PCT_STAT_N_HULL_VOXELS = 6,   /* voxels inside the hull mask */
@@ -121,7 +124,8 @@ enum pct_stat {
     PCT_STAT_ROW_BYTES = 8,       /* device bytes of the stored rows */
     PCT_STAT_BATCH_CTA = 9,       /* threads per CTA of the last batched solve */
     PCT_STAT_BATCH_CTAS = 10,     /* CTAs of the last batched solve */
-    PCT_STAT_GRAPH_REPLAYS = 11   /* batched solves replayed from a CUDA graph */
+    PCT_STAT_GRAPH_REPLAYS = 11,  /* batched solves replayed from a CUDA graph */
+    PCT_STAT_TIMED_LAUNCHES = 12  /* launches of the DROP block kernel timed (PCT_OPT_TIMING) */
 };
 
 /* Create a context on CUDA device `device`.

@@ -537,7 +537,8 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
         c->mem_cap = value;
         return PCT_OK;
     case PCT_OPT_TIMING:
-        c->timing = value ? 1 : 0;
+        if (value < 0 || value > 0x7fffffff) return fail(c, PCT_ERR_ARG, "timing period must be >= 0");
+        c->timing = (int)value;
         return PCT_OK;
     case PCT_OPT_GRAPH:
         c->graph = value ? 1 : 0;
@@ -746,7 +747,7 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
         for (int64_t first = 0; first < c->n; first += block_size) {
             const int64_t count = block_size < c->n - first ? block_size : c->n - first;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (c->timing) {
+            if (c->timing > 0 && c->fused_launches % c->timing == 0) {
                 e0 = next_event(c);
                 e1 = next_event(c);
                 if (e0) cudaEventRecord(e0, c->stream);
@@ -1085,6 +1086,7 @@ pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
     switch (key) {
     case PCT_STAT_LAUNCHES: *value = (double)c->launches; return PCT_OK;
     case PCT_STAT_FUSED_LAUNCHES: *value = (double)c->fused_launches; return PCT_OK;
+    case PCT_STAT_TIMED_LAUNCHES: *value = (double)(c->ev_used / 2); return PCT_OK;
     case PCT_STAT_FUSED_MS: {
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "stream");

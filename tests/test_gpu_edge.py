@@ -43,6 +43,30 @@ def test_errors_and_states(cuda_device):
     ctx.close()
 
 
+def test_sampled_launch_timing(cuda_device):
+    cfg, rsp, hull, hist = U.scan("tiny")
+    ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull)
+    ctx.load_histories({k: torch.from_numpy(v).cuda() for k, v in hist.items()})
+    x = torch.from_numpy(hull.astype(np.float32)).cuda()
+    with pytest.raises(pct.PctError) as e:
+        ctx.set_option(pct.PCT_OPT_TIMING, -1)
+    assert e.value.status == pct.PCT_ERR_ARG
+    blocks = math.ceil(cfg.n_protons / cfg.block)
+    for period in (1, 3):
+        ctx.reset_stats()
+        ctx.set_option(pct.PCT_OPT_TIMING, period)
+        ctx.solve(x, 2, cfg.lam, cfg.block)
+        launches = ctx.stat(pct.PCT_STAT_FUSED_LAUNCHES)
+        assert launches == 2 * blocks
+        assert ctx.stat(pct.PCT_STAT_TIMED_LAUNCHES) == math.ceil(launches / period)
+        assert ctx.stat(pct.PCT_STAT_FUSED_MS) > 0
+    ctx.reset_stats()
+    ctx.set_option(pct.PCT_OPT_TIMING, 0)
+    ctx.solve(x, 1, cfg.lam, cfg.block)
+    assert ctx.stat(pct.PCT_STAT_TIMED_LAUNCHES) == 0 and ctx.stat(pct.PCT_STAT_FUSED_MS) == 0
+    ctx.close()
+
+
 def test_memory_cap_gives_oom_status(cuda_device):
     cfg, rsp, hull, hist = U.scan("tiny")
     ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull)
