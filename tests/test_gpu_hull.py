@@ -67,3 +67,36 @@ def test_distance_caps_at_255():
 def test_empty_and_full_hull():
     assert (_gpu_dist(np.zeros((4, 5, 6), np.uint8)) == 255).all()
     assert (_gpu_dist(np.ones((4, 5, 6), np.uint8)) == 0).all()
+
+
+def test_hull_entry_on_a_non_convex_hull_matches_oracle():
+    """Hull entry and exit through a hollow shell, a one-voxel wall and isolated
+    voxels: the skipping search must stop at the same first hull voxel as the
+    oracle's voxel-by-voxel search (thin features are where a jump too long
+    would show)."""
+    import oracle as O
+    from tests import parity_util as U
+    cfg, rsp, hull, hist = U.scan("tiny", 30000)
+    nx, ny, nz = cfg.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    cx, cy = x - nx / 2 + 0.5, y - ny / 2 + 0.5
+    r = np.hypot(cx, cy)
+    mask = ((r >= 20) & (r <= 28)) | (x == 10)
+    rng = np.random.default_rng(5)
+    for _ in range(40):
+        mask[rng.integers(0, nz), rng.integers(0, ny), rng.integers(0, nx)] = True
+    mask = mask.astype(np.uint8).reshape(-1)
+    ctx = U.context(cfg, mask, hist)
+    st = ctx.hull_states().cpu().numpy().astype(np.float64)
+    ctx.close()
+    geo = U.geometry(cfg, mask)
+    ost, ovalid, omargin = O.prepare(geo, hist)
+    gvalid = st[:, 10] > 0.5
+    mism = np.flatnonzero(gvalid != ovalid)
+    assert np.all(omargin[mism] < U.NEAR_FACE_MM), mism[:10]
+    both = gvalid & ovalid
+    assert both.sum() > 0.5 * len(gvalid)
+    for col in (0, 1, 2, 4, 6, 8):
+        d = np.abs(st[both, col] - ost[both, col])
+        ok = (d <= U.MLP_TOL_MM) | (omargin[both] < U.NEAR_FACE_MM)
+        assert ok.all(), (col, d.max())
