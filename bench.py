@@ -138,18 +138,21 @@ def fused_flops(n_valid, mean_pts, mean_nnz):
     return (samples * FLOP_PER_SAMPLE + segs * FLOP_PER_SEGMENT + mean_nnz * FLOP_PER_VISIT) * n_valid
 
 
+# the sources the fused block kernel is compiled from (host code excluded)
+KERNEL_SOURCES = ("pct_device.cuh", "pct_kernels.cu", "pct_warp.cuh")
+
+
 def _kernel_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1802_01070_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _profiled_traffic(workload):
-    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
-    if it was taken on the current kernel source; else None."""
+    """The committed ncu summary of the fused kernel (DRAM bytes per valid row,
+    issue rate), if it was taken on the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "drop_fused_traffic.json")
     try:
         d = json.load(open(path))
@@ -158,7 +161,7 @@ def _profiled_traffic(workload):
     if d.get("kernel_hash") != _kernel_hash():
         return None
     per_row = d.get("dram_bytes_per_valid_row")
-    return per_row if per_row else None
+    return d if per_row else None
 
 
 def _measured_peaks():
@@ -364,7 +367,8 @@ def run_ours(args):
     flops_launch = fused_flops(valid, mean_pts, mean_nnz) / blocks_per_iter
     achieved = flops_launch / avg_launch_s / 1e12
     hbm_bytes_launch = (n / blocks_per_iter) * (16 * 4)        # proton records streamed per launch
-    per_row_traffic = _profiled_traffic(cfg.name) if args.mode == "fused" else None
+    prof = _profiled_traffic(cfg.name) if args.mode == "fused" else None
+    per_row_traffic = prof["dram_bytes_per_valid_row"] if prof else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": (per_row_traffic * valid / blocks_per_iter) if per_row_traffic else None,
@@ -375,6 +379,12 @@ def run_ours(args):
                                "per valid row" % (max(mean_pts - 2, 0), FLOP_PER_SAMPLE,
                                                   max(mean_pts - 1, 0), FLOP_PER_SEGMENT, mean_nnz,
                                                   FLOP_PER_VISIT),
+                "issue_frac_profiled": (prof["issue_ipc_per_sm"] / prof["issue_ipc_peak"]
+                                        if prof and "issue_ipc_per_sm" in prof else None),
+                "issue_note": "the kernel is bound by instruction issue (integer/compare/branch work "
+                              "of the voxel walk), not FP32 math: issued warp instructions per SM "
+                              "cycle over the 4 the SM can issue, from the committed ncu capture of "
+                              "this kernel source (profiles/drop_fused_torso_block320k.md)",
                 "hbm_gbs_algorithmic": hbm_bytes_launch / avg_launch_s / 1e9,
                 "hbm_peak_gbs": peaks.get("hbm_gbs"),
                 "fused_share_of_step": avg_launch_s * 1e3 * fused_n / args.steps / step_ms
