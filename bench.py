@@ -50,6 +50,8 @@ def _args():
                         "reconstruction with the differentiable projector (workload 'diff')")
     p.add_argument("--mode", default="fused", choices=["fused", "csr", "packed"],
                    help="row form: recomputed on the fly, or stored (built once, timed apart)")
+    p.add_argument("--chord", default="fixed16", choices=["fixed16", "fp16"],
+                   help="chord code of the packed rows")
     p.add_argument("--cpu-sample", type=int, default=320000)
     p.add_argument("--ref-sample", type=int, default=100000)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -291,6 +293,8 @@ def run_ours(args):
         ctx.set_option(pct.PCT_OPT_CTA_THREADS, args.cta)
     mode = {"fused": pct.PCT_MODE_FUSED, "csr": pct.PCT_MODE_CSR, "packed": pct.PCT_MODE_PACKED}[args.mode]
     ctx.set_option(pct.PCT_OPT_MODE, mode)
+    ctx.set_option(pct.PCT_OPT_CHORD_CODE,
+                   pct.PCT_CHORD_FIXED16 if args.chord == "fixed16" else pct.PCT_CHORD_FP16)
     ctx.load_histories(hist)
     build_s = None
     if mode != pct.PCT_MODE_FUSED:
@@ -410,7 +414,9 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": dict(_config(cfg, block, n), mode=args.mode), "recon_s": step_ms * 1e-3,
+           "config": dict(_config(cfg, block, n), mode=args.mode,
+                          **({"chord": args.chord} if args.mode == "packed" else {})),
+           "recon_s": step_ms * 1e-3,
            "row_build_s": build_s, "row_bytes": ctx.stat(pct.PCT_STAT_ROW_BYTES),
            "row_entries": ctx.stat(pct.PCT_STAT_ROW_ENTRIES),
            "rows_in_hull": valid, "mean_nnz_per_row": mean_nnz, "mean_mlp_points": mean_pts,
@@ -446,6 +452,7 @@ def run_ours(args):
         xo, dt, vs, threads = oracle_solve_timed(cfg, hull_np, sub_np, cfg.iters, cfg.lam, block)
         with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=local) as c2:
             c2.set_option(pct.PCT_OPT_MODE, mode)
+            c2.set_option(pct.PCT_OPT_CHORD_CODE, ctx.get_option(pct.PCT_OPT_CHORD_CODE))
             c2.load_histories(sub)
             xg = torch.from_numpy(hull_np.astype(np.float32)).to(dev)
             c2.solve(xg, cfg.iters, cfg.lam, block)

@@ -96,7 +96,10 @@ enum pct_option {
     /* Test only: 1 = the first barrier of the batch's first scan waits for one
      * arrival more than its CTAs make, so the wait runs out (exercises the
      * timeout path without any fault).  Default 0. */
-    PCT_OPT_TEST_UNREACHABLE_BARRIER = 9
+    PCT_OPT_TEST_UNREACHABLE_BARRIER = 9,
+    /* Chord code of PCT_MODE_PACKED rows (one of enum pct_chord_code).  Default
+     * PCT_CHORD_FIXED16.  Changing it drops packed rows. */
+    PCT_OPT_CHORD_CODE = 10
 };
 
 /* Row forms of pct_solve.  The stored forms are built by the same walk as the
@@ -107,8 +110,17 @@ enum pct_mode {
     PCT_MODE_FUSED = 0,  /* recompute MLP and walk for every row of every block: no storage */
     PCT_MODE_CSR = 1,    /* int64 row offsets + int32 voxel + FP32 chord per entry (8 B) */
     PCT_MODE_PACKED = 2  /* int64 row offsets + first voxel per row + per entry a 1-byte 3D step
-                            code with an in-hull bit and an FP16 chord (3 B); runs outside the
-                            hull are kept (weight 0) so that steps stay between neighbours */
+                            code with an in-hull bit and a 16-bit chord (PCT_OPT_CHORD_CODE) (3 B);
+                            runs outside the hull are kept (weight 0) so that steps stay between
+                            neighbours */
+};
+
+/* 16-bit chord codes of packed rows.  A run's chord lies inside one voxel. */
+enum pct_chord_code {
+    PCT_CHORD_FIXED16 = 0,  /* unsigned fixed point in units of 1.25 x the voxel diagonal / 65535
+                               (1 mm voxels: 3.3e-5 mm, rounding error <= 1.7e-5 mm); a chord
+                               beyond the range is clamped and flagged (PCT_ERR_DEVICE) */
+    PCT_CHORD_FP16 = 1      /* IEEE half precision (relative rounding <= 2^-11) */
 };
 
 /* Keys of pct_get_stat.  Counters cover the calls since pct_reset_stats. */

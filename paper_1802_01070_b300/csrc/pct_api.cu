@@ -59,7 +59,8 @@ struct pct_ctx {
     int32_t* d_idx = nullptr;
     float* d_len = nullptr;
     uint8_t* d_codes = nullptr;
-    void* d_lens16 = nullptr;
+    uint16_t* d_lens16 = nullptr;
+    int chord_code = PCT_CHORD_FIXED16;    // packed chords: fixed point or FP16
     short4* d_start = nullptr;
     int cta = 256;
     int timing = 0;
@@ -271,11 +272,22 @@ pct_status compact(pct_ctx* c, int64_t B)
     return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "valid-proton lists");
 }
 
+// Unit of the packed rows' 16-bit fixed-point chords (mm), 0 for FP16 chords.
+// A run's chord lies in one voxel: up to the voxel diagonal, a little more
+// where the polyline bends inside the voxel; 1.25 diagonals span the code.
+float chord_unit(const pct_ctx* c)
+{
+    if (c->chord_code != PCT_CHORD_FIXED16) return 0.f;
+    const double diag = std::sqrt((double)c->grid.dx * c->grid.dx + (double)c->grid.dy * c->grid.dy +
+                                  (double)c->grid.dz * c->grid.dz);
+    return (float)(1.25 * diag / 65535.0);
+}
+
 int64_t row_bytes(const pct_ctx* c)
 {
     int64_t b = 0;
     for (void* p : {(void*)c->d_rowptr, (void*)c->d_idx, (void*)c->d_len, (void*)c->d_codes,
-                    c->d_lens16, (void*)c->d_start}) {
+                    (void*)c->d_lens16, (void*)c->d_start}) {
         auto it = c->sizes.find(p);
         if (p && it != c->sizes.end()) b += (int64_t)it->second;
     }
@@ -358,10 +370,11 @@ pct_status build_rows(pct_ctx* c)
     if (c->mode == PCT_MODE_PACKED) {
         if ((s = dalloc(c, &p, ne, "packed row codes")) == PCT_OK) {
             c->d_codes = (uint8_t*)p;
-            if ((s = dalloc(c, &p, ne * 2, "packed row chords")) == PCT_OK) c->d_lens16 = p;
+            if ((s = dalloc(c, &p, ne * 2, "packed row chords")) == PCT_OK) c->d_lens16 = (uint16_t*)p;
         }
         if (s == PCT_OK)
-            e = launch_pack_fill(L, G, c->d_rec, c->stride, m, c->d_rowptr, c->d_codes, c->d_lens16);
+            e = launch_pack_fill(L, G, c->d_rec, c->stride, m, c->d_rowptr, c->d_codes, c->d_lens16,
+                                 chord_unit(c));
     } else {
         if ((s = dalloc(c, &p, ne * sizeof(int32_t), "CSR indices")) == PCT_OK) {
             c->d_idx = (int32_t*)p;
@@ -559,6 +572,11 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
         if ((int)value != c->mode) drop_rows(c);
         c->mode = (int)value;
         return PCT_OK;
+    case PCT_OPT_CHORD_CODE:
+        if (value != PCT_CHORD_FIXED16 && value != PCT_CHORD_FP16) return fail(c, PCT_ERR_ARG, "unknown chord code");
+        if ((int)value != c->chord_code && c->mode == PCT_MODE_PACKED) drop_rows(c);
+        c->chord_code = (int)value;
+        return PCT_OK;
     default:
         return fail(c, PCT_ERR_ARG, "unknown option key");
     }
@@ -573,6 +591,7 @@ pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
     case PCT_OPT_MEM_CAP_BYTES: *value = c->mem_cap; return PCT_OK;
     case PCT_OPT_TIMING: *value = c->timing; return PCT_OK;
     case PCT_OPT_MODE: *value = c->mode; return PCT_OK;
+    case PCT_OPT_CHORD_CODE: *value = c->chord_code; return PCT_OK;
     case PCT_OPT_GRAPH: *value = c->graph; return PCT_OK;
     case PCT_OPT_AUTOTUNE: *value = c->autotune; return PCT_OK;
     case PCT_OPT_SPIN_LIMIT: *value = c->spin_limit; return PCT_OK;
@@ -756,7 +775,8 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
             if (c->mode == PCT_MODE_CSR)
                 e = launch_drop_csr(L, c->d_flags, c->d_rowptr, c->d_idx, c->d_len, b, first, count, x, c->d_acc);
             else if (c->mode == PCT_MODE_PACKED)
-                e = launch_drop_packed(L, c->gc, c->d_flags, c->d_rowptr, c->d_start, c->d_codes, c->d_lens16, b,
+                e = launch_drop_packed(L, c->gc, c->d_flags, c->d_rowptr, c->d_start, c->d_codes, c->d_lens16,
+                                       chord_unit(c), b,
                                        first, count, x, c->d_acc);
             else
                 e = launch_drop_fused(L, G, c->d_rec, c->stride, c->d_vidx, c->d_boff, first / block_size,
@@ -1074,6 +1094,7 @@ pct_status pct_synchronize(pct_ctx* c)
         if (flags & kFlagRowSlots) m += " a row too long for pct_rows (nnz reported as -1);";
         if (flags & kFlagPackStep) m += " packed rows: non-neighbouring consecutive voxels;";
         if (flags & kFlagRowBounds) m += " stored row length or voxel index out of range;";
+        if (flags & kFlagChordRange) m += " packed rows: a chord beyond the fixed-point range (clamped);";
         return fail(c, PCT_ERR_DEVICE, m);
     }
     return PCT_OK;

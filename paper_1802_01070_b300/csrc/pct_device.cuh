@@ -34,6 +34,7 @@ constexpr unsigned kFlagMlpTable = 4u;    // MLP sample index beyond the S1 tabl
 constexpr unsigned kFlagRowSlots = 8u;    // a debug row had more runs per lane than its slots
 constexpr unsigned kFlagPackStep = 16u;   // packed rows: consecutive runs not in neighbouring voxels
 constexpr unsigned kFlagRowBounds = 32u;  // a stored row's length or voxel index out of range
+constexpr unsigned kFlagChordRange = 128u; // packed rows: a chord beyond the fixed-point range (clamped)
 constexpr unsigned kFlagBarrierTimeout = 64u;  // a bounded barrier wait gave up
 
 struct GridC {

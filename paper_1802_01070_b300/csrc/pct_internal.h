@@ -78,16 +78,18 @@ cudaError_t launch_csr_fill(const Launch& L, const Geo& G, const float* rec, int
                             int64_t m, const int64_t* rowptr, int32_t* idx, float* len);
 cudaError_t launch_pack_count(const Launch& L, const Geo& G, const float* rec, int64_t stride,
                               int64_t m, int32_t* cnt, short4* start);
+// chord_unit > 0: 16-bit fixed-point chords in units of chord_unit mm; 0: FP16
 cudaError_t launch_pack_fill(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                             int64_t m, const int64_t* rowptr, uint8_t* codes, void* lens);
+                             int64_t m, const int64_t* rowptr, uint8_t* codes, uint16_t* lens,
+                             float chord_unit);
 cudaError_t launch_row_scan(const Launch& L, const int32_t* cnt, int64_t m, int64_t* rowptr,
                             int64_t* chunk_sum);
 cudaError_t launch_drop_csr(const Launch& L, unsigned* flags, const int64_t* rowptr, const int32_t* idx,
                             const float* len, const float* b, int64_t first, int64_t count,
                             const float* x, float2* acc);
 cudaError_t launch_drop_packed(const Launch& L, const GridC& g, unsigned* flags, const int64_t* rowptr,
-                               const short4* start, const uint8_t* codes, const void* lens,
-                               const float* b, int64_t first, int64_t count, const float* x,
-                               float2* acc);
+                               const short4* start, const uint8_t* codes, const uint16_t* lens,
+                               float chord_unit, const float* b, int64_t first, int64_t count,
+                               const float* x, float2* acc);
 
 }  // namespace pct

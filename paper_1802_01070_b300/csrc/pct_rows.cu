@@ -194,7 +194,8 @@ struct PackWriter {
     const uint8_t* __restrict__ mask;
     unsigned* flags;
     uint8_t* codes;
-    __half* lens;
+    uint16_t* lens;
+    float unit_inv;        // 16-bit fixed-point chords in units of 1/unit_inv mm; 0: FP16
     int64_t off, end;
     int px, py, pz;        // voxel of the previous written entry
     bool have_prev;        // px.. valid (false only for the row's very first run)
@@ -219,9 +220,20 @@ struct PackWriter {
                 code = (uint8_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
         }
         if (g.inside(qx, qy, qz) && __ldg(mask + g.index(qx, qy, qz))) code |= kCodeInside;
+        uint16_t u;
+        if (unit_inv > 0.f) {
+            float v = l * unit_inv;
+            if (v > 65535.f) {
+                atomicOr(flags, kFlagChordRange);
+                v = 65535.f;
+            }
+            u = (uint16_t)__float2uint_rn(v);
+        } else {
+            u = __half_as_ushort(__float2half_rn(l));
+        }
         if (off < end) {
             codes[off] = code;
-            lens[off] = __float2half_rn(l);
+            lens[off] = u;
         }
         ++off;
         px = qx;
@@ -246,7 +258,7 @@ struct PackWriter {
 __global__ void __launch_bounds__(kRowCta)
 k_pack_fill(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
             int64_t m, const int64_t* __restrict__ rowptr, uint8_t* __restrict__ codes,
-            __half* __restrict__ lens)
+            uint16_t* __restrict__ lens, float unit_inv)
 {
     const int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= m) return;
@@ -264,7 +276,7 @@ k_pack_fill(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsi
     if (k0 >= k1) return;
     // a lane other than the first codes its first run as a step from the previous
     // lane's last voxel; the row's first run is the "start" entry
-    PackWriter w{Dims{g.nx, g.ny, g.nz}, mask, flags, codes, lens, off, rowptr[i + 1], pm.px, pm.py,
+    PackWriter w{Dims{g.nx, g.ny, g.nz}, mask, flags, codes, lens, unit_inv, off, rowptr[i + 1], pm.px, pm.py,
                  pm.pz, lane > 0, pm.merged_prev, pm.next_merges ? pm.next_hl : 0.f, 0, 0, 0, 0.f,
                  false, true};
     walk_points(P, mc, g, flags, k0, k1, ends, w);
@@ -394,7 +406,7 @@ k_drop_csr(unsigned* flags, const int64_t* __restrict__ rowptr, const int32_t* _
 // Decode 32 packed entries starting at e0 into voxels (warp-cooperative): the
 // steps are prefix-summed across the lanes.
 __device__ __forceinline__ void unpack32(const uint8_t* __restrict__ codes,
-                                         const __half* __restrict__ lens, int64_t e0, int64_t e1,
+                                         const uint16_t* __restrict__ lens, float unit, int64_t e0, int64_t e1,
                                          int& bx, int& by, int& bz, const Dims& g, int& j, float& l,
                                          bool& inside)
 {
@@ -402,7 +414,8 @@ __device__ __forceinline__ void unpack32(const uint8_t* __restrict__ codes,
     const int64_t e = e0 + lane;
     const bool valid = e < e1;
     const int code = valid ? (int)__ldg(codes + e) : (int)kCodeStart;
-    l = valid ? __half2float(lens[e]) : 0.f;
+    const uint16_t raw = valid ? lens[e] : (uint16_t)0;
+    l = unit > 0.f ? (float)raw * unit : __half2float(__ushort_as_half(raw));
     const int st = code & 31;
     const int dx = st % 3, dy = (st / 3) % 3, dz = st / 9;   // each 0..2 (step + 1)
     int p = dx | (dy << 10) | (dz << 20);
@@ -423,7 +436,7 @@ __device__ __forceinline__ void unpack32(const uint8_t* __restrict__ codes,
 
 __global__ void __launch_bounds__(kRowCta)
 k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, const short4* __restrict__ start,
-              const uint8_t* __restrict__ codes, const __half* __restrict__ lens,
+              const uint8_t* __restrict__ codes, const uint16_t* __restrict__ lens, float unit,
               const float* __restrict__ b, int64_t first, int64_t count,
               const float* __restrict__ x, float2* acc)
 {
@@ -445,7 +458,7 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
         int j;
         float l;
         bool in;
-        unpack32(codes, lens, e0, e1, bx, by, bz, g, j, l, in);
+        unpack32(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
         if (in && (unsigned)j >= (unsigned)nvox) {
             atomicOr(flags, kFlagRowBounds);
             in = false;
@@ -469,7 +482,7 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
         int j;
         float l;
         bool in;
-        unpack32(codes, lens, e0, e1, bx, by, bz, g, j, l, in);
+        unpack32(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
         if (in && (unsigned)j < (unsigned)nvox) atomicAdd(acc + j, make_float2(l * r, 1.f));
     }
 }
@@ -517,11 +530,13 @@ cudaError_t launch_pack_count(const Launch& L, const Geo& G, const float* rec, i
 }
 
 cudaError_t launch_pack_fill(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                             int64_t m, const int64_t* rowptr, uint8_t* codes, void* lens)
+                             int64_t m, const int64_t* rowptr, uint8_t* codes, uint16_t* lens,
+                             float chord_unit)
 {
     if (m <= 0) return cudaSuccess;
+    const float unit_inv = chord_unit > 0.f ? 1.f / chord_unit : 0.f;
     k_pack_fill<<<rows_grid(m), kRowCta, 0, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
-                                                        G.flags, m, rowptr, codes, (__half*)lens);
+                                                        G.flags, m, rowptr, codes, lens, unit_inv);
     PCT_ROWS_TAIL(L);
 }
 
@@ -552,14 +567,13 @@ cudaError_t launch_drop_csr(const Launch& L, unsigned* flags, const int64_t* row
 }
 
 cudaError_t launch_drop_packed(const Launch& L, const GridC& g, unsigned* flags, const int64_t* rowptr,
-                               const short4* start, const uint8_t* codes, const void* lens,
-                               const float* b, int64_t first, int64_t count, const float* x,
-                               float2* acc)
+                               const short4* start, const uint8_t* codes, const uint16_t* lens,
+                               float chord_unit, const float* b, int64_t first, int64_t count,
+                               const float* x, float2* acc)
 {
     if (count <= 0) return cudaSuccess;
-    k_drop_packed<<<rows_grid(count), kRowCta, 0, L.stream>>>(g, flags, rowptr, start, codes,
-                                                              (const __half*)lens, b, first, count, x,
-                                                              acc);
+    k_drop_packed<<<rows_grid(count), kRowCta, 0, L.stream>>>(g, flags, rowptr, start, codes, lens,
+                                                              chord_unit, b, first, count, x, acc);
     PCT_ROWS_TAIL(L);
 }
 

@@ -1,9 +1,10 @@
-"""Stored row forms (CSR; packed 1-byte step codes + FP16 chords) through the C ABI.
+"""Stored row forms (CSR; packed 1-byte step codes + 16-bit chords) through the C ABI.
 
 The stored rows are built by the walk of the fused path, so the CSR solve must
 equal the fused solve up to the order of FP32 atomics, and both match the
-FP64 oracle; the packed form carries FP16 chords, and its RSP error against
-the oracle is measured and bounded.
+FP64 oracle; the packed form carries 16-bit chords (fixed point of the voxel
+diagonal, or FP16), and its RSP error against the oracle is measured and
+bounded for each code.
 """
 import numpy as np
 import pytest
@@ -56,24 +57,50 @@ def test_csr_solve_equals_fused_solve_and_oracle(tiny, lam):
     assert (rel <= 1e-3).mean() >= 0.99 and rel.mean() <= 1e-4
 
 
-def test_packed_solve_error_against_fp64(tiny):
+@pytest.mark.parametrize("code", ["fixed16", "fp16"])
+def test_packed_solve_error_against_fp64(tiny, code):
     cfg, ctx, hull = tiny["cfg"], tiny["ctx"], tiny["hull"]
+    ctx.set_option(pct.PCT_OPT_CHORD_CODE,
+                   pct.PCT_CHORD_FIXED16 if code == "fixed16" else pct.PCT_CHORD_FP16)
     xp = _solve(ctx, hull, pct.PCT_MODE_PACKED, cfg.iters, 0.5, cfg.block)
     entries = int(ctx.stat(pct.PCT_STAT_ROW_ENTRIES))
     nbytes = ctx.stat(pct.PCT_STAT_ROW_BYTES)
     xf = _solve(ctx, hull, pct.PCT_MODE_FUSED, cfg.iters, 0.5, cfg.block)
+    ctx.set_option(pct.PCT_OPT_CHORD_CODE, pct.PCT_CHORD_FIXED16)
     xo = O.drop(tiny["A"], tiny["hist"]["wepl"].astype(np.float64), cfg.iters, 0.5, cfg.block,
                 hull.astype(np.float64))
     hm = hull.astype(bool)
     rp = np.abs(xp - xo)[hm] / np.abs(xo)[hm]
     rf = np.abs(xf - xo)[hm] / np.abs(xo)[hm]
-    print("packed: %d entries, %.2f B/entry; rel err vs FP64 max %.3g mean %.3g (fused: max %.3g "
-          "mean %.3g)" % (entries, nbytes / max(entries, 1), rp.max(), rp.mean(), rf.max(), rf.mean()))
-    # FP16 chords carry a relative rounding of 2^-12: the RSP moves by about that much
-    assert rp.mean() <= 5e-4 and (rp <= 1e-2).mean() >= 0.999
+    print("packed (%s chords): %d entries, %.2f B/entry; rel err vs FP64 max %.3g mean %.3g "
+          "(fused: max %.3g mean %.3g)" % (code, entries, nbytes / max(entries, 1), rp.max(), rp.mean(),
+                                           rf.max(), rf.mean()))
+    if code == "fp16":
+        # FP16 chords carry a relative rounding of up to 2^-11: the RSP moves by about that much
+        assert rp.mean() <= 5e-4 and (rp <= 1e-2).mean() >= 0.999
+    else:
+        # fixed-point chords (~1.7e-5 mm) keep the FP32 path's accuracy
+        assert rp.mean() <= 2e-5 and (rp <= 1e-3).mean() >= 0.999 and rp.max() <= 1e-2
     assert nbytes / max(entries, 1) < 4.0
     # packed rows keep runs outside the hull too: at least as many entries as CSR rows
     assert entries >= tiny["rowptr"][-1] - 1000
+
+
+def test_chord_code_option(cuda_device):
+    cfg, rsp, hull, hist = U.scan("tiny")
+    h = {k: np.ascontiguousarray(v[:3000]) for k, v in hist.items()}
+    ctx = U.context(cfg, hull, h)
+    assert ctx.get_option(pct.PCT_OPT_CHORD_CODE) == pct.PCT_CHORD_FIXED16
+    with pytest.raises(pct.PctError) as e:
+        ctx.set_option(pct.PCT_OPT_CHORD_CODE, 7)
+    assert e.value.status == pct.PCT_ERR_ARG
+    ctx.set_option(pct.PCT_OPT_MODE, pct.PCT_MODE_PACKED)
+    ctx.build_rows()
+    assert ctx.stat(pct.PCT_STAT_ROW_ENTRIES) > 0
+    ctx.set_option(pct.PCT_OPT_CHORD_CODE, pct.PCT_CHORD_FP16)
+    assert ctx.stat(pct.PCT_STAT_ROW_ENTRIES) == 0          # a new chord code drops packed rows
+    assert ctx.get_option(pct.PCT_OPT_CHORD_CODE) == pct.PCT_CHORD_FP16
+    ctx.close()
 
 
 def test_stored_rows_ragged_blocks_and_invalidation(cuda_device):
