@@ -2,7 +2,7 @@
 //   CSR:    int64 row offsets, int32 voxel index and FP32 chord per entry (8 B);
 //   packed: int64 row offsets, the first run's voxel per row, and per entry a
 //           one-byte code (3D step to the entry's voxel from the previous one,
-//           plus an in-hull bit) and an FP16 chord (3 B).
+//           plus an in-hull bit) and a 16-bit chord, fixed point or FP16 (3 B).
 // Both are built by the warp walk of the fused path, so their rows are the
 // fused rows; the packed form keeps the runs outside the hull too, so that
 // consecutive entries are always neighbouring voxels.
