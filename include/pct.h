@@ -216,6 +216,13 @@ pct_status pct_hull_distance(pct_ctx *ctx, uint8_t *out_dist);
 pct_status pct_mlp(pct_ctx *ctx, int64_t first, int64_t count, int32_t max_pts, float *out_xyz,
                    int32_t *out_npts);
 
+/* The calls below that walk paths (pct_hull_states, pct_mlp, pct_rows,
+ * pct_forward, pct_adjoint, pct_solve, pct_build_rows) first compute the
+ * per-proton records of the loaded histories (beam frame, hull entry and exit
+ * of the tracker lines, entry and exit states; kernel k_prepare) if they are
+ * not yet computed, and keep them until new histories are loaded or the MLP
+ * step changes. */
+
 /* Rows of A for protons [first, first+count), in path order: each entry is one
  * visit of the MLP polyline to a hull voxel (a maximal run of the path inside
  * that voxel) with its chord length a_ij in mm.

@@ -41,6 +41,7 @@ struct pct_ctx {
     unsigned* d_flags = nullptr;
     unsigned long long* d_next = nullptr;   // work counter of the fused block step
     bool loaded = false;                 // pct_load_histories has succeeded once
+    bool rec_valid = false;              // the records match the loaded histories and MLP step
     int64_t n = 0, stride = 0, cap = 0;  // protons, column stride, column capacity
     float* d_hist = nullptr;
     float* d_rec = nullptr;
@@ -228,11 +229,14 @@ pct_status need_histories(pct_ctx* c)
     return PCT_OK;
 }
 
+// Per-proton records (hull entry/exit, beam frame, FP64-evaluated states):
+// computed once per loaded history set and MLP step, kept until either changes.
 pct_status prepare(pct_ctx* c)
 {
-    if (c->n == 0) return PCT_OK;
+    if (c->n == 0 || c->rec_valid) return PCT_OK;
     cudaError_t e = launch_prepare(launch_of(c), geo_of(c), c->d_hist, c->stride, c->n, c->d_rec);
     if (e != cudaSuccess) return cuda_fail(c, e, "prepare kernel");
+    c->rec_valid = true;
     return PCT_OK;
 }
 
@@ -539,6 +543,7 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
     case PCT_OPT_MLP_STEP_UM: {
         if (value < 0 || value > 100000) return fail(c, PCT_ERR_ARG, "MLP step out of range");
         drop_rows(c);
+        c->rec_valid = false;
         const int64_t old = c->du_um;
         c->du_um = value;
         pct_status s = build_sigma_table(c);
@@ -609,6 +614,7 @@ pct_status pct_load_histories(pct_ctx* c, int64_t n, const float* const in_xyz[3
     if (n < 0) return fail(c, PCT_ERR_ARG, "negative proton count");
     DeviceGuard dg(c->device);
     drop_rows(c);
+    c->rec_valid = false;
     if (n == 0) {
         c->n = 0;
         c->loaded = true;
