@@ -727,7 +727,7 @@ pct_status pct_forward(pct_ctx* c, const float* x, float* y)
     pct_status s = need_histories(c);
     if (s == PCT_OK) s = prepare(c);
     if (s != PCT_OK) return s;
-    cudaError_t e = launch_forward(launch_of(c), geo_of(c), c->d_rec, c->stride, c->n, x, y);
+    cudaError_t e = launch_forward(launch_of(c), geo_of(c), c->d_rec, c->stride, c->n, x, y, c->d_next);
     return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "forward kernel");
 }
 
@@ -741,7 +741,7 @@ pct_status pct_adjoint(pct_ctx* c, const float* y, float* g)
     if (s != PCT_OK) return s;
     cudaError_t e = cudaMemsetAsync(g, 0, (size_t)c->n_vox * sizeof(float), c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint clear");
-    e = launch_adjoint(launch_of(c), geo_of(c), c->d_rec, c->stride, c->n, y, g);
+    e = launch_adjoint(launch_of(c), geo_of(c), c->d_rec, c->stride, c->n, y, g, c->d_next);
     return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "adjoint kernel");
 }
 

@@ -42,10 +42,12 @@ cudaError_t launch_mlp_points(const Launch& L, const Geo& G, const float* rec, i
 cudaError_t launch_rows(const Launch& L, const Geo& G, const float* rec, int64_t stride,
                         int64_t first, int64_t count, int32_t max_nnz, int32_t* out_idx,
                         float* out_len, int32_t* out_nnz);
+// y = A x and g += A^T y (g cleared by the caller); `next` is a device work
+// counter, cleared by the launcher.
 cudaError_t launch_forward(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                           int64_t n, const float* x, float* y);
+                           int64_t n, const float* x, float* y, unsigned long long* next);
 cudaError_t launch_adjoint(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                           int64_t n, const float* y, float* g_out);
+                           int64_t n, const float* y, float* g_out, unsigned long long* next);
 // Lists of the protons whose path crosses the hull, per DROP block of size B:
 // block k's protons are vidx[boff[k] .. boff[k+1]) (proton order).  chunk is
 // scratch of compact_chunks(n) values; vidx holds n values, boff

@@ -247,58 +247,75 @@ k_rows(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned*
     if (lane == 0) nnz[t] = total;
 }
 
-// y = A x (a10), one warp per row, no atomics.
+// Work distribution of the warp-per-proton kernels: the grid has one warp per
+// item up to filling the GPU once.  Each warp takes a first chunk of `first`
+// items by its index (kGrab when there are at least kGrab items per warp of
+// the grid, else 1) and, while items are left, chunks of kGrab items from the
+// counter *next (zero at launch), so that warps whose paths were short take
+// more of them and the launch ends evenly.  body(t) runs on the whole warp.
+constexpr int kGrab = 2;
+
+template <class F>
+__device__ __forceinline__ void for_each_item(int64_t count, int first, unsigned long long* next, F&& body)
+{
+    const int64_t stat = (int64_t)gridDim.x * (blockDim.x >> 5) * first;   // items assigned by index
+    const int lane = threadIdx.x & (kWarp - 1);
+    int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * first;
+    int64_t end = base + first;
+    while (base < count) {
+        end = end < count ? end : count;
+        for (int64_t t = base; t < end; ++t) body(t);
+        if (stat >= count) break;   // every item was assigned by index
+        unsigned long long got = 0;
+        if (lane == 0) got = atomicAdd(next, (unsigned long long)kGrab);
+        base = stat + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+        end = base + kGrab;
+    }
+}
+
+// y = A x (a10), one warp per row, no atomics; y is cleared beforehand, rows
+// without a hull path are skipped.
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_forward(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
-          int64_t n, const float* __restrict__ x, float* __restrict__ y)
+          int64_t n, const float* __restrict__ x, float* __restrict__ y, unsigned long long* next,
+          int first)
 {
     extern __shared__ unsigned char smem[];
-    const int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    Path P;
-    if (!load_path(rv, i, mc, P)) {
-        if ((threadIdx.x & 31) == 0) y[i] = 0.f;
-        return;
-    }
-    LaneWalk w;
-    float s, q;
-    warp_walk<0, true>(P, mc, g, mask, x, flags, warp_slots(smem, 0), mc.cmin, w, s, q);
-    if ((threadIdx.x & 31) == 0) y[i] = s;
+    for_each_item(n, first, next, [&](int64_t i) {
+        Path P;
+        if (!load_path(rv, i, mc, P)) return;
+        LaneWalk w;
+        float s, q;
+        warp_walk<0, true>(P, mc, g, mask, x, flags, warp_slots(smem, 0), mc.cmin, w, s, q);
+        if ((threadIdx.x & 31) == 0) y[i] = s;
+    });
 }
 
 // g = A^T y (a10), one warp per row, scatter by FP32 atomics.
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
-          int64_t n, const float* __restrict__ y, float* gout)
+          int64_t n, const float* __restrict__ y, float* gout, unsigned long long* next, int first)
 {
     extern __shared__ unsigned char smem[];
-    const int64_t i = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const float yi = __ldg(y + i);
-    if (yi == 0.f) return;
-    Path P;
-    if (!load_path(rv, i, mc, P)) return;
     const RunSlots slots = warp_slots(smem, kRunSlots);
-    LaneWalk w;
-    float s, q;
-    warp_walk<kRunSlots, false>(P, mc, g, mask, nullptr, flags, slots, mc.cmin, w, s, q);
-    replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
-                           [&](int j, float l) { atomicAdd(gout + j, l * yi); });
+    for_each_item(n, first, next, [&](int64_t i) {
+        const float yi = __ldg(y + i);
+        if (yi == 0.f) return;
+        Path P;
+        if (!load_path(rv, i, mc, P)) return;
+        LaneWalk w;
+        float s, q;
+        warp_walk<kRunSlots, false>(P, mc, g, mask, nullptr, flags, slots, mc.cmin, w, s, q);
+        replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
+                               [&](int j, float l) { atomicAdd(gout + j, l * yi); });
+    });
 }
 
 // DROP block step (a3-a6 fused), one warp per proton of the block, x frozen:
 //   r_i = (b_i - a_i.x) / ||a_i||^2, then acc[j] += (a_ij r_i, 1) over its row.
 // The row is walked once; the scatter replays the runs kept in shared memory.
 // The block's protons are the entries vidx[boff[k] .. boff[k+1]) of the list
-// of protons whose path crosses the hull (the others have empty rows).  The
-// grid has one warp per proton up to filling the GPU once.  Each warp takes a
-// first chunk of `first` protons by its index (kGrab when the block holds at
-// least kGrab protons per warp of the grid, else 1) and, while protons are
-// left, chunks of kGrab protons from the counter *next (zero at launch), so
-// that warps whose paths were short take more of them and the launch ends
-// evenly.
-constexpr int kGrab = 2;
-
+// of protons whose path crosses the hull (the others have empty rows).
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
              const int64_t* __restrict__ vidx, const int64_t* __restrict__ boff, int64_t k,
@@ -306,31 +323,19 @@ k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, uns
 {
     extern __shared__ unsigned char smem[];
     const RunSlots slots = warp_slots(smem, kRunSlots);
-    const int64_t lo = boff[k], count = boff[k + 1] - lo;
-    const int64_t stat = (int64_t)gridDim.x * (blockDim.x >> 5) * first;   // protons assigned by index
-    const int lane = threadIdx.x & (kWarp - 1);
-    int64_t base = (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)) * first;
-    int64_t end = base + first;
-    while (base < count) {
-        end = end < count ? end : count;
-        for (int64_t t = base; t < end; ++t) {
-            const int64_t i = vidx[lo + t];
-            Path P;
-            if (!load_path(rv, i, mc, P)) continue;
-            LaneWalk w;
-            float s, q;
-            warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
-            if (!(q > 0.f)) continue;
-            const float r = (rv.get(R_B, i) - s) / q;
-            replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
-                                   [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
-        }
-        if (stat >= count) break;   // the whole block was assigned by index
-        unsigned long long got = 0;
-        if (lane == 0) got = atomicAdd(next, (unsigned long long)kGrab);
-        base = stat + (int64_t)__shfl_sync(0xffffffffu, got, 0);
-        end = base + kGrab;
-    }
+    const int64_t lo = boff[k];
+    for_each_item(boff[k + 1] - lo, first, next, [&](int64_t t) {
+        const int64_t i = vidx[lo + t];
+        Path P;
+        if (!load_path(rv, i, mc, P)) return;
+        LaneWalk w;
+        float s, q;
+        warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
+        if (!(q > 0.f)) return;
+        const float r = (rv.get(R_B, i) - s) / q;
+        replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
+                               [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
+    });
 }
 
 // DROP block apply (a7): x_j += lambda * num_j / s_j where the block touched
@@ -437,24 +442,62 @@ cudaError_t launch_rows(const Launch& L, const Geo& G, const float* rec, int64_t
     PCT_LAUNCH_TAIL(L);
 }
 
+// Launch shape of a warp-per-item kernel over `count` items: one warp per item
+// up to the CTAs that fill the GPU once (resident CTAs per SM x SMs, cached
+// per thread, device and CTA size), and the first chunk per warp.
+template <class K>
+cudaError_t item_shape(K kernel, int cta, size_t smem, int64_t count, unsigned& grid, int& first)
+{
+    thread_local const void* fill_kernel = nullptr;
+    thread_local int fill_dev = -1, fill_cta = -1, fill = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (fill_kernel != (const void*)kernel || fill_dev != dev || fill_cta != cta) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, cta, smem);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        fill = per_sm * sms;
+        fill_kernel = (const void*)kernel;
+        fill_dev = dev;
+        fill_cta = cta;
+    }
+    grid = warp_grid(count, cta);
+    if (fill > 0 && grid > (unsigned)fill) grid = (unsigned)fill;
+    const int64_t warps = (int64_t)grid * (cta / kWarp);
+    first = count >= (int64_t)kGrab * warps ? kGrab : 1;
+    return cudaSuccess;
+}
+
 cudaError_t launch_forward(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                           int64_t n, const float* x, float* y)
+                           int64_t n, const float* x, float* y, unsigned long long* next)
 {
     if (n <= 0) return cudaSuccess;
-    k_forward<<<warp_grid(n, L.cta), L.cta, 0, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
-                                                           G.flags, n, x, y);
+    unsigned grid;
+    int first;
+    cudaError_t e = item_shape(k_forward, L.cta, 0, n, grid, first);
+    if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, (size_t)n * sizeof(float), L.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), L.stream);
+    if (e != cudaSuccess) return e;
+    k_forward<<<grid, L.cta, 0, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, n, x, y,
+                                            next, first);
     PCT_LAUNCH_TAIL(L);
 }
 
 cudaError_t launch_adjoint(const Launch& L, const Geo& G, const float* rec, int64_t stride,
-                           int64_t n, const float* y, float* g_out)
+                           int64_t n, const float* y, float* g_out, unsigned long long* next)
 {
     if (n <= 0) return cudaSuccess;
     const size_t sm = slot_bytes(L.cta, kRunSlots);
     cudaError_t e = allow_smem(k_adjoint, sm);
+    unsigned grid;
+    int first;
+    if (e == cudaSuccess) e = item_shape(k_adjoint, L.cta, sm, n, grid, first);
+    if (e == cudaSuccess) e = cudaMemsetAsync(next, 0, sizeof(unsigned long long), L.stream);
     if (e != cudaSuccess) return e;
-    k_adjoint<<<warp_grid(n, L.cta), L.cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
-                                                            G.flags, n, y, g_out);
+    k_adjoint<<<grid, L.cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, n, y,
+                                             g_out, next, first);
     PCT_LAUNCH_TAIL(L);
 }
 
@@ -464,30 +507,13 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
 {
     if (count <= 0) return cudaSuccess;
     const size_t sm = slot_bytes(L.cta, kRunSlots);
-    auto kernel = k_drop_fused;
-    cudaError_t e = allow_smem(kernel, sm);
+    cudaError_t e = allow_smem(k_drop_fused, sm);
+    unsigned grid;
+    int first;
+    if (e == cudaSuccess) e = item_shape(k_drop_fused, L.cta, sm, count, grid, first);
     if (e != cudaSuccess) return e;
-    unsigned grid = warp_grid(count, L.cta);
-    // fill the GPU exactly once (resident CTAs per SM x SMs); warps stride
-    // over the block's protons, so no partial wave is left at the tail
-    thread_local int fill_dev = -1, fill_cta = -1, fill = 0;
-    int dev = 0;
-    e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (fill_dev != dev || fill_cta != L.cta) {
-        int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, L.cta, sm);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        fill = per_sm * sms;
-        fill_dev = dev;
-        fill_cta = L.cta;
-    }
-    if (fill > 0 && grid > (unsigned)fill) grid = (unsigned)fill;
-    const int64_t warps = (int64_t)grid * (L.cta / kWarp);
-    const int first = count >= (int64_t)kGrab * warps ? kGrab : 1;
-    kernel<<<grid, L.cta, sm, L.stream>>>(
-        G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff, k, x, acc, next, first);
+    k_drop_fused<<<grid, L.cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff,
+                                                k, x, acc, next, first);
     PCT_LAUNCH_TAIL(L);
 }
 
