@@ -33,6 +33,32 @@ __device__ __forceinline__ double plane_crossing(const GridC& g, const double T[
     return (fma((double)face, d, o) - T[axis]) / D[axis];
 }
 
+// tan t of a tracker angle.  For |t| <= 0.25 rad (nearly every proton) the
+// Maclaurin series tan t = sum_n T_n t^(2n-1), T_n = (-1)^(n-1) 2^(2n)
+// (2^(2n) - 1) B_2n / (2n)! with B the Bernoulli numbers, summed to 11 terms
+// in Horner form in t^2 (relative error <= 2.2e-16 on that range, checked
+// against 40-digit arithmetic); larger angles take the library tan.
+__device__ __forceinline__ double tan_angle(double t)
+{
+    if (!(fabs(t) <= 0.25)) return tan(t);
+    constexpr double T[11] = {1.0,
+                              1.0 / 3.0,
+                              2.0 / 15.0,
+                              17.0 / 315.0,
+                              62.0 / 2835.0,
+                              1382.0 / 155925.0,
+                              21844.0 / 6081075.0,
+                              929569.0 / 638512875.0,
+                              6404582.0 / 10854718875.0,
+                              443861162.0 / 1856156927625.0,
+                              18888466084.0 / 194896477400625.0};
+    const double t2 = t * t;
+    double a = T[10];
+#pragma unroll
+    for (int k = 9; k >= 0; --k) a = fma(a, t2, T[k]);
+    return a * t;
+}
+
 __global__ void __launch_bounds__(kMaxCta)
 k_prepare(GridC g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ dist, unsigned* flags,
           const float* __restrict__ h,
@@ -67,7 +93,7 @@ k_prepare(GridC g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__
     // the record, evaluated once in FP64 from the raw inputs and the crossed planes
     double sd, cd;
     sincos((double)phi, &sd, &cd);
-    const double ti = tan((double)thi), pi = tan((double)psi), to = tan((double)tho), po = tan((double)pso);
+    const double ti = tan_angle(thi), pi = tan_angle(psi), to = tan_angle(tho), po = tan_angle(pso);
     const double Ti[3] = {xi, yi, zi}, To[3] = {xo, yo, zo};
     const double Di[3] = {fma(-ti, sd, cd), fma(ti, cd, sd), pi};
     const double Do[3] = {-fma(-to, sd, cd), -fma(to, cd, sd), -po};
