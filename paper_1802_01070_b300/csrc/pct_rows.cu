@@ -387,7 +387,26 @@ k_drop_csr(unsigned* flags, const int64_t* __restrict__ rowptr, const int32_t* _
     }
     const int lane = threadIdx.x & 31;
     float s = 0.f, q = 0.f;
-    for (int64_t e = a + lane; e < e1; e += kWarp) {
+    // four entries per lane in flight at a time (the loop is latency-bound);
+    // each lane still sums its entries in increasing order
+    int64_t e = a + lane;
+    for (; e + 3 * kWarp < e1; e += 4 * kWarp) {
+        int j[4];
+        float l[4], xv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = __ldg(idx + e + u * kWarp);
+            l[u] = __ldg(len + e + u * kWarp);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xv[u] = __ldg(x + j[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            s = fmaf(l[u], xv[u], s);
+            q = fmaf(l[u], l[u], q);
+        }
+    }
+    for (; e < e1; e += kWarp) {
         const float l = __ldg(len + e);
         s = fmaf(l, __ldg(x + __ldg(idx + e)), s);
         q = fmaf(l, l, q);
@@ -399,7 +418,19 @@ k_drop_csr(unsigned* flags, const int64_t* __restrict__ rowptr, const int32_t* _
     }
     if (!(q > 0.f)) return;
     const float r = (__ldg(b + i) - s) / q;
-    for (int64_t e = a + lane; e < e1; e += kWarp)
+    e = a + lane;
+    for (; e + 3 * kWarp < e1; e += 4 * kWarp) {
+        int j[4];
+        float l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = __ldg(idx + e + u * kWarp);
+            l[u] = __ldg(len + e + u * kWarp);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) atomicAdd(acc + j[u], make_float2(l[u] * r, 1.f));
+    }
+    for (; e < e1; e += kWarp)
         atomicAdd(acc + __ldg(idx + e), make_float2(__ldg(len + e) * r, 1.f));
 }
 
