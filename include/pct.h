@@ -180,8 +180,10 @@ pct_status pct_get_option(const pct_ctx *ctx, int32_t key, int64_t *value);
  *                     t = (-sin phi, cos phi, 0), v = z
  *   wepl_mm        -- measured WEPL (b of A x = b), mm
  * ptrs_on_device = 1: all pointers are device pointers (copied on the stream,
- * asynchronously); 0: host pointers (copied, then the call synchronizes, so
- * the host buffers may be reused on return; pinned buffers copy fastest).
+ * asynchronously); 0: host pointers (copied in chunks on an internal stream,
+ * the per-proton records of each chunk computed on the context stream as it
+ * lands; the call returns when the copies are done, so the host buffers may be
+ * reused on return; pinned buffers copy fastest and overlap best).
  * The library keeps its own copy; the caller keeps ownership.  n = 0 is valid.
  * Errors: PCT_ERR_ARG (n < 0 or a null pointer with n > 0), PCT_ERR_OOM,
  * PCT_ERR_CUDA. */

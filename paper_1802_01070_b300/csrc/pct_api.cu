@@ -1,6 +1,7 @@
 // pct_api.cu -- the C ABI of libpct (declared in include/pct.h): context
 // lifetime, device memory, history upload, and the host-side loops that drive
 // the kernels of pct_kernels.cu.  No call aborts or throws across the ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,6 +81,10 @@ struct pct_ctx {
     int* d_abort = nullptr;
     int scan_cap = 0;
     cudaStream_t batch_stream = nullptr;
+    // uploads from host memory: copy stream and one event per uploaded chunk
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t copy_ready = nullptr;
+    std::vector<cudaEvent_t> chunk_ev;
     cudaEvent_t batch_ev[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<int64_t> graph_key;
@@ -228,6 +233,9 @@ pct_status need_histories(pct_ctx* c)
     if (!c->loaded) return fail(c, PCT_ERR_STATE, "no proton histories loaded");
     return PCT_OK;
 }
+
+// Protons per chunk of an upload from host memory.
+constexpr int64_t kUploadChunk = 1 << 22;
 
 // Per-proton records (hull entry/exit, beam frame, FP64-evaluated states):
 // computed once per loaded history set and MLP step, kept until either changes.
@@ -522,6 +530,10 @@ void pct_destroy(pct_ctx* c)
     for (cudaEvent_t e : c->batch_ev)
         if (e) cudaEventDestroy(e);
     if (c->batch_stream) cudaStreamDestroy(c->batch_stream);
+    for (cudaEvent_t e : c->chunk_ev)
+        if (e) cudaEventDestroy(e);
+    if (c->copy_ready) cudaEventDestroy(c->copy_ready);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -649,18 +661,56 @@ pct_status pct_load_histories(pct_ctx* c, int64_t n, const float* const in_xyz[3
         c->cap = stride;
     }
     c->stride = stride;
-    const cudaMemcpyKind kind = ptrs_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    for (int f = 0; f < H_NF; ++f) {
-        cudaError_t e = cudaMemcpyAsync(c->d_hist + (size_t)f * stride, src[f], (size_t)n * sizeof(float),
-                                        kind, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "history copy");
+    if (ptrs_on_device) {
+        for (int f = 0; f < H_NF; ++f) {
+            cudaError_t e = cudaMemcpyAsync(c->d_hist + (size_t)f * stride, src[f], (size_t)n * sizeof(float),
+                                            cudaMemcpyDeviceToDevice, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "history copy");
+        }
+        c->n = n;
+        c->loaded = true;
+        return PCT_OK;
     }
-    if (!ptrs_on_device) {
-        cudaError_t e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "history copy");
-    }
+    // From host memory: upload in chunks on the copy stream (after the work
+    // already on the context stream) and prepare each chunk's records on the
+    // context stream as soon as it has landed, so the record kernel runs under
+    // the rest of the upload.
+    cudaError_t e = cudaSuccess;
+    if (!c->copy_stream) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !c->copy_ready) e = cudaEventCreateWithFlags(&c->copy_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(c->copy_ready, c->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c->copy_stream, c->copy_ready, 0);
+    if (e != cudaSuccess) return cuda_fail(c, e, "upload stream");
     c->n = n;
     c->loaded = true;
+    c->rec_valid = false;
+    const int64_t nchunk = (n + kUploadChunk - 1) / kUploadChunk;
+    while ((int64_t)c->chunk_ev.size() < nchunk) {
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "upload events");
+        c->chunk_ev.push_back(ev);
+    }
+    const Launch L = launch_of(c);
+    const Geo G = geo_of(c);
+    for (int64_t k = 0; k < nchunk && e == cudaSuccess; ++k) {
+        const int64_t a = k * kUploadChunk, cnt = std::min(kUploadChunk, n - a);
+        for (int f = 0; f < H_NF && e == cudaSuccess; ++f)
+            e = cudaMemcpyAsync(c->d_hist + (size_t)f * stride + a, src[f] + a, (size_t)cnt * sizeof(float),
+                                cudaMemcpyHostToDevice, c->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(c->chunk_ev[(size_t)k], c->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->chunk_ev[(size_t)k], 0);
+        if (e == cudaSuccess) e = launch_prepare_range(L, G, c->d_hist, stride, a, cnt, c->d_rec);
+    }
+    // the host buffers may be reused once the copies are done
+    cudaError_t es = cudaStreamSynchronize(c->copy_stream);
+    if (e == cudaSuccess) e = es;
+    if (e != cudaSuccess) {
+        c->loaded = false;
+        c->n = 0;
+        return cuda_fail(c, e, "history upload");
+    }
+    c->rec_valid = true;
     return PCT_OK;
 }
 

@@ -34,6 +34,9 @@ cudaError_t launch_hull_dist(const Launch& L, const uint8_t* mask, int nx, int n
                              uint8_t* dist);
 cudaError_t launch_prepare(const Launch& L, const Geo& G, const float* hist, int64_t stride,
                            int64_t n, float* rec);
+// records of protons [first, first + count) only
+cudaError_t launch_prepare_range(const Launch& L, const Geo& G, const float* hist, int64_t stride,
+                                 int64_t first, int64_t count, float* rec);
 cudaError_t launch_hull_states(const Launch& L, const float* rec, int64_t stride, int64_t first,
                                int64_t count, float* out);
 cudaError_t launch_mlp_points(const Launch& L, const Geo& G, const float* rec, int64_t stride,

@@ -390,17 +390,23 @@ __global__ void k_drop_apply(int64_t n_vox, float* __restrict__ x, float2* __res
         return cudaGetLastError(); \
     } while (0)
 
-cudaError_t launch_prepare(const Launch& L, const Geo& G, const float* hist, int64_t stride,
-                           int64_t n, float* rec)
+cudaError_t launch_prepare_range(const Launch& L, const Geo& G, const float* hist, int64_t stride,
+                                 int64_t first, int64_t count, float* rec)
 {
-    if (n <= 0) return cudaSuccess;
+    if (count <= 0) return cudaSuccess;
     const float diag = sqrtf((float)G.g.nx * G.g.dx * (float)G.g.nx * G.g.dx +
                              (float)G.g.ny * G.g.dy * (float)G.g.ny * G.g.dy +
                              (float)G.g.nz * G.g.dz * (float)G.g.nz * G.g.dz);
     const float Lmax = fminf(diag * 1.0001f + 1e-3f, (float)(G.mc.kmax - 2) * G.mc.du_mm);
-    k_prepare<<<grid_for(n, L.cta), L.cta, 0, L.stream>>>(G.g, G.mask, G.dist, G.flags, hist, stride, 0,
-                                                          n, rec, Lmax);
+    k_prepare<<<grid_for(count, L.cta), L.cta, 0, L.stream>>>(G.g, G.mask, G.dist, G.flags, hist, stride,
+                                                              first, count, rec, Lmax);
     PCT_LAUNCH_TAIL(L);
+}
+
+cudaError_t launch_prepare(const Launch& L, const Geo& G, const float* hist, int64_t stride,
+                           int64_t n, float* rec)
+{
+    return launch_prepare_range(L, G, hist, stride, 0, n, rec);
 }
 
 cudaError_t launch_hull_dist(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, uint8_t* tmp,

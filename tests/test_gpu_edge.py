@@ -67,6 +67,29 @@ def test_sampled_launch_timing(cuda_device):
     ctx.close()
 
 
+def test_host_upload_in_chunks_matches_device_load(cuda_device):
+    """Histories from (pinned) host memory are uploaded in chunks of 2^22 protons
+    with each chunk's records prepared as it lands: the records and a solve
+    equal those of a device-to-device load."""
+    cfg = synth.scaled(synth.CONFIGS["tiny"], (1 << 22) + 12345)
+    rsp, hull = synth.phantom(cfg)
+    hist = synth.histories(cfg, cuda_device, rsp=rsp)
+    host = {k: v.cpu().pin_memory() for k, v in hist.items()}
+    hull = hull.numpy()
+    x0 = torch.from_numpy(hull.astype(np.float32)).cuda()
+    out = []
+    for h in (hist, host):
+        with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull) as ctx:
+            ctx.load_histories(h)
+            st = ctx.hull_states().clone()
+            x = x0.clone()
+            ctx.solve(x, 1, cfg.lam, 320000)
+            ctx.synchronize()
+            out.append((st, x))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.allclose(out[0][1], out[1][1], rtol=1e-5, atol=1e-6)   # FP32 atomics order
+
+
 def test_memory_cap_gives_oom_status(cuda_device):
     cfg, rsp, hull, hist = U.scan("tiny")
     ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull)
