@@ -1,8 +1,10 @@
 // pct_kernels.cu -- CUDA kernels of libpct and their launchers (sm_103a).
 //
-// All per-proton kernels map one proton to one thread (arXiv:1802.01070,
-// Sec. I) and recompute the proton's row of A from its record: MLP samples,
-// then the voxel walk (pct_device.cuh).  None of them stores A.
+// The record kernel maps one proton to one thread, as arXiv:1802.01070 maps
+// every proton (Sec. I); the kernels that walk paths map one proton to one
+// warp (pct_warp.cuh) and recompute the proton's row of A from its record:
+// MLP samples, then the voxel walk.  None of them stores A.  Also here: the
+// valid-proton lists of the DROP blocks and the hull distance map.
 #include "pct_internal.h"
 #include "pct_warp.cuh"
 
@@ -18,7 +20,7 @@ inline unsigned grid_for(int64_t n, int cta)
 }
 
 // ---------------------------------------------------------------------------
-// Hull-frame record of each proton (a2): rotate the tracker data into the
+// Hull-frame record of each proton: rotate the tracker data into the
 // beam frame of its gantry angle, follow both straight tracker lines to the
 // hull, and store the entry/exit states the MLP starts from.
 // ---------------------------------------------------------------------------
@@ -213,7 +215,8 @@ k_mlp_points(GridC g, MlpC mc, RecView rv, int64_t first, int64_t count, int32_t
 // Runs a lane can keep in shared memory: DROP / adjoint passes, and the debug
 // row writer (which must not fall back).
 constexpr int kRunSlots = 24;
-// warp-per-proton kernels: at most 256 threads per CTA, 64 registers per thread
+// warp-per-proton kernels: at most 256 threads per CTA, 3 CTAs per SM (80
+// registers per thread, no spills: measured faster than 4 CTAs with spills)
 constexpr int kWarpCta = 256;
 constexpr int kWarpCtaMin = 3;
 constexpr int kRowSlots = 64;
@@ -299,7 +302,7 @@ __device__ __forceinline__ void for_each_item(int64_t count, int first, unsigned
     }
 }
 
-// y = A x (a10), one warp per row, no atomics; y is cleared beforehand, rows
+// y = A x, one warp per row, no atomics; y is cleared beforehand, rows
 // without a hull path are skipped.
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_forward(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
@@ -317,7 +320,7 @@ k_forward(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsign
     });
 }
 
-// g = A^T y (a10), one warp per row, scatter by FP32 atomics.
+// g = A^T y, one warp per row, scatter by FP32 atomics.
 __global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
 k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
           int64_t n, const float* __restrict__ y, float* gout, unsigned long long* next, int first)
@@ -337,7 +340,8 @@ k_adjoint(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsign
     });
 }
 
-// DROP block step (a3-a6 fused), one warp per proton of the block, x frozen:
+// DROP block step (Sec. IV-B; MLP, walk, row dot and scatter fused), one warp
+// per proton of the block, x frozen:
 //   r_i = (b_i - a_i.x) / ||a_i||^2, then acc[j] += (a_ij r_i, 1) over its row.
 // The row is walked once; the scatter replays the runs kept in shared memory.
 // The block's protons are the entries vidx[boff[k] .. boff[k+1]) of the list
@@ -364,7 +368,7 @@ k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, uns
     });
 }
 
-// DROP block apply (a7): x_j += lambda * num_j / s_j where the block touched
+// DROP block apply (Sec. IV-B): x_j += lambda * num_j / s_j where the block touched
 // voxel j, and clear the accumulator for the next block.
 // `next` (if not null): the work counter of the block step, reset here for
 // the next block step on the stream.
