@@ -40,7 +40,7 @@ struct pct_ctx {
     int kmax = 0;
     int64_t du_um = 0;
     unsigned* d_flags = nullptr;
-    unsigned long long* d_next = nullptr;   // work counter of the fused block step
+    unsigned long long* d_next = nullptr;   // work counter of the warp-per-proton kernels
     bool loaded = false;                 // pct_load_histories has succeeded once
     bool rec_valid = false;              // the records match the loaded histories and MLP step
     int64_t n = 0, stride = 0, cap = 0;  // protons, column stride, column capacity
