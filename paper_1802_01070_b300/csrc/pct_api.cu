@@ -79,6 +79,7 @@ struct pct_ctx {
     ScanDesc* d_scans = nullptr;
     unsigned* d_bar = nullptr;
     int* d_abort = nullptr;
+    unsigned long long* d_bnext = nullptr;   // per-scan work counters
     int scan_cap = 0;
     cudaStream_t batch_stream = nullptr;
     // uploads from host memory: copy stream and one event per uploaded chunk
@@ -911,6 +912,7 @@ pct_status enqueue_batch(pct_ctx* c0, pct_ctx* const* ctxs, int32_t count, const
     const Launch L0{stream, c0->cta, launches};
     cudaError_t e = cudaMemsetAsync(c0->d_bar, 0, sizeof(unsigned) * count, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c0->d_abort, 0, sizeof(int) * count, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c0->d_bnext, 0, sizeof(unsigned long long) * count, stream);
     for (int32_t k = 0; k < count && e == cudaSuccess; ++k) {
         pct_ctx* c = ctxs[k];
         if (c->n == 0) continue;
@@ -955,9 +957,11 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
         dfree(c0, c0->d_scans);
         dfree(c0, c0->d_bar);
         dfree(c0, c0->d_abort);
+        dfree(c0, c0->d_bnext);
         c0->d_scans = nullptr;
         c0->d_bar = nullptr;
         c0->d_abort = nullptr;
+        c0->d_bnext = nullptr;
         c0->scan_cap = 0;
         void* p = nullptr;
         pct_status s = dalloc(c0, &p, sizeof(ScanDesc) * count, "batch descriptors");
@@ -967,6 +971,8 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
         c0->d_bar = (unsigned*)p;
         if ((s = dalloc(c0, &p, sizeof(int) * count, "batch abort flags")) != PCT_OK) return s;
         c0->d_abort = (int*)p;
+        if ((s = dalloc(c0, &p, sizeof(unsigned long long) * count, "batch work counters")) != PCT_OK) return s;
+        c0->d_bnext = (unsigned long long*)p;
         c0->scan_cap = count;
     }
     if (!c0->batch_stream) {
@@ -1024,6 +1030,7 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
             d.ncta = share;
             d.bar = c0->d_bar + k;
             d.abort = c0->d_abort + k;
+            d.next = c0->d_bnext + k;
             used += share;
         }
         *total_out = used;

@@ -13,6 +13,11 @@
 //
 // x and the accumulator are rewritten inside the launch by other CTAs, so they
 // are read through L2 only (ld.global.cg) and written back the same way.
+//
+// Within a block step the scan's warps take one or two protons by index and
+// then chunks from the scan's work counter, so that the barrier after the step
+// does not wait for one unlucky warp; the scan's first thread resets the
+// counter between the two barriers of the block.
 #include "pct_batch.h"
 #include "pct_warp.cuh"
 
@@ -21,6 +26,7 @@ namespace pct {
 namespace {
 
 constexpr int kBatchRunSlots = 24;
+constexpr int kBatchGrab = 2;
 
 __device__ __forceinline__ bool scan_barrier(const ScanDesc& d, int* abort_flag, unsigned* flags,
                                              int spin_limit, int extra_target)
@@ -70,26 +76,41 @@ k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int
     const RecView rv{d.rec, d.stride};
     // only the first barrier of scan 0 is made unreachable by the test option
     int extra = (test_unreachable && s == 0) ? 1 : 0;
+    const int lane = threadIdx.x & 31;
     for (int it = 0; it < d.iters; ++it) {
         for (int64_t first = 0; first < d.n; first += d.block) {
             const int64_t count = d.block < d.n - first ? d.block : d.n - first;
-            for (int64_t p = warp_in_scan; p < count; p += nwarp) {
-                const int64_t i = first + p;
-                Path P;
-                if (!load_path(rv, i, d.mc, P)) continue;
-                LaneWalk w;
-                float sv, q;
-                warp_walk<kBatchRunSlots, true, true>(P, d.mc, d.g, d.mask, d.x, flags, slots, d.mc.cmin,
-                                                      w, sv, q);
-                if (!(q > 0.f)) continue;
-                const float r = (rv.get(R_B, i) - sv) / q;
-                float2* acc = d.acc;
-                replay_runs<kBatchRunSlots>(P, d.mc, d.g, d.mask, flags, slots, w, [&](int j, float l) {
-                    atomicAdd(acc + j, make_float2(l * r, 1.f));
-                });
+            const int per = count >= (int64_t)kBatchGrab * nwarp ? kBatchGrab : 1;
+            const int64_t stat = (int64_t)nwarp * per;   // protons assigned by index
+            int64_t base = (int64_t)warp_in_scan * per, end = base + per;
+            while (base < count) {
+                end = end < count ? end : count;
+                for (int64_t p = base; p < end; ++p) {
+                    const int64_t i = first + p;
+                    Path P;
+                    if (!load_path(rv, i, d.mc, P)) continue;
+                    LaneWalk w;
+                    float sv, q;
+                    warp_walk<kBatchRunSlots, true, true>(P, d.mc, d.g, d.mask, d.x, flags, slots, d.mc.cmin,
+                                                          w, sv, q);
+                    if (!(q > 0.f)) continue;
+                    const float r = (rv.get(R_B, i) - sv) / q;
+                    float2* acc = d.acc;
+                    replay_runs<kBatchRunSlots>(P, d.mc, d.g, d.mask, flags, slots, w, [&](int j, float l) {
+                        atomicAdd(acc + j, make_float2(l * r, 1.f));
+                    });
+                }
+                if (stat >= count) break;
+                unsigned long long got = 0;
+                if (lane == 0) got = atomicAdd(d.next, (unsigned long long)kBatchGrab);
+                base = stat + (int64_t)__shfl_sync(0xffffffffu, got, 0);
+                end = base + kBatchGrab;
             }
             if (!scan_barrier(d, abort_flag, flags, spin_limit, extra)) return;
             extra = 0;
+            // every warp of the scan is past its block step: reset the counter for
+            // the next one (ordered before it by the barrier below)
+            if (tid_in_scan == 0) atomicExch(d.next, 0ull);
             for (int64_t j = tid_in_scan; j < d.n_vox; j += nthr) {
                 const float2 a = __ldcg(d.acc + j);
                 if (a.y > 0.f) {

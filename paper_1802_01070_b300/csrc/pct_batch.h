@@ -21,6 +21,7 @@ struct ScanDesc {
     int cta0, ncta;       // CTA range of the scan
     unsigned* bar;        // barrier arrival counter (zero on entry)
     int* abort;           // set when a barrier wait of the scan gave up (zero on entry)
+    unsigned long long* next;   // work counter of the scan's block steps (zero on entry)
 };
 
 size_t batch_smem(int cta);
