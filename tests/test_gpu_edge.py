@@ -90,6 +90,31 @@ def test_host_upload_in_chunks_matches_device_load(cuda_device):
     assert torch.allclose(out[0][1], out[1][1], rtol=1e-5, atol=1e-6)   # FP32 atomics order
 
 
+def test_records_follow_histories_and_mlp_step(cuda_device):
+    """The per-proton records are kept between calls: a repeated call reuses
+    them, a new MLP step or a new history load recomputes them."""
+    cfg, rsp, hull, hist = U.scan("tiny")
+    a, b = _sub(hist, 0, 3000), _sub(hist, 3000, 6000)
+    ctx = U.context(cfg, hull, a)
+    st_a = ctx.hull_states().clone()
+    ctx.reset_stats()
+    _, n1 = ctx.mlp(0, 100, max_pts=1024)
+    launches = ctx.stat(pct.PCT_STAT_LAUNCHES)
+    assert launches == 1                                  # the MLP kernel alone: records kept
+    ctx.set_option(pct.PCT_OPT_MLP_STEP_UM, 500)
+    _, n2 = ctx.mlp(0, 100, max_pts=1024)
+    ok = n1 > 0
+    assert torch.all(n2[ok] > n1[ok])                     # finer step, records recomputed
+    ctx.set_option(pct.PCT_OPT_MLP_STEP_UM, 1000)
+    ctx.load_histories({k: torch.from_numpy(v).cuda() for k, v in b.items()})
+    st_b = ctx.hull_states()
+    ref = U.context(cfg, hull, b)
+    assert torch.equal(st_b, ref.hull_states())           # the new histories' records
+    assert not torch.equal(st_a, st_b)
+    ref.close()
+    ctx.close()
+
+
 def test_memory_cap_gives_oom_status(cuda_device):
     cfg, rsp, hull, hist = U.scan("tiny")
     ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull)
