@@ -4,9 +4,12 @@
 Workload (default): torso-sized scan, 280x280x96 grid of 1 mm voxels, 1.16e8
 synthetic protons over 180 gantry angles in 2-degree steps, 6 DROP iterations,
 block size 320000, rows recomputed on the fly (A never stored), FP32.
-One step = one pct_solve from the initial iterate (x0 = 1 inside the hull):
-hull entry of every proton, then 6 iterations of per-block fused MLP + walk +
-dot + scatter and the block apply.
+One step = one reconstruction from the device-resident histories: load them
+(device-to-device copy), then pct_solve from the initial iterate (x0 = 1 inside
+the hull): per-proton records (hull entry/exit) and valid-proton lists, then 6
+iterations of per-block fused MLP + walk + dot + scatter and the block apply.
+With --mode csr|packed a step is the solve over rows built once beforehand
+(the build is timed apart: row_build_s).
 
 Prints ONE JSON line (rank 0).  `value` is proton-rows/s per iteration (rows =
 protons whose path crosses the hull), summed over ranks; `recon_s` is the
@@ -245,14 +248,21 @@ def run_reference(args):
     return 0
 
 
-def _config(cfg, block, n):
+FORM_TEXT = {"fused": "fused on-the-fly MLP+walk (A never stored)",
+             "csr": "rows stored as CSR (int32 voxel + FP32 chord per entry), built once",
+             "packed": "rows stored packed (1-byte step code + 16-bit chord per entry), built once"}
+
+
+def _config(cfg, block, n, mode="fused"):
     return {"workload": "%s: %dx%dx%d grid of %g mm voxels, %d protons over %d angles, %d DROP "
-                        "iterations, block %d, fused on-the-fly MLP+walk (A never stored)"
-                        % (cfg.name, *cfg.shape, cfg.voxel, n, cfg.n_angles, cfg.iters, block),
+                        "iterations, block %d, %s"
+                        % (cfg.name, *cfg.shape, cfg.voxel, n, cfg.n_angles, cfg.iters, block,
+                           FORM_TEXT[mode]),
             "grid": list(cfg.shape), "voxel_mm": cfg.voxel, "protons": n, "angles": cfg.n_angles,
             "iters": cfg.iters, "block": block, "lambda": cfg.lam, "x0": "1.0 inside hull",
-            "l2": "inputs larger than L2: 48 B of history and 64 B of record per proton are "
-                  "streamed each pass (%.1f GB)" % (n * 112 / 1e9)}
+            "l2": "inputs larger than L2: 48 B of history per proton read each step and 72 B of "
+                  "record + list entry per crossing proton streamed each iteration (%.1f GB of "
+                  "histories and records)" % (n * 112 / 1e9)}
 
 
 # ----------------------------------------------------------------------------
@@ -420,7 +430,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": dict(_config(cfg, block, n), mode=args.mode,
+           "config": dict(_config(cfg, block, n, args.mode), mode=args.mode,
                           **({"chord": args.chord} if args.mode == "packed" else {})),
            "recon_s": step_ms * 1e-3,
            "row_build_s": build_s, "row_bytes": ctx.stat(pct.PCT_STAT_ROW_BYTES),
