@@ -13,6 +13,7 @@ import scipy.integrate as si
 import scipy.sparse as sp
 
 import oracle as O
+import synth
 
 pytestmark = pytest.mark.filterwarnings("ignore::DeprecationWarning")
 
@@ -396,6 +397,46 @@ def test_drop_consistent_data_fixed_point_and_convergence():
         errs.append(np.linalg.norm(x - xs))
     assert all(e1 <= e0 + 1e-12 for e0, e1 in zip(errs, errs[1:]))
     assert errs[-1] < 0.2 * np.linalg.norm(np.ones(A.shape[1]) - xs)
+
+
+def _proton_system(n=4000):
+    """Rows of synthetic protons through the tiny phantom, and its RSP."""
+    cfg = synth.scaled(synth.CONFIGS["tiny"], n)
+    rsp, hull = synth.phantom(cfg)
+    hist = synth.to_numpy(synth.histories(cfg, "cpu", rsp=rsp))
+    geo = O.Geometry(cfg.shape, (cfg.voxel,) * 3, cfg.origin, mask=hull.numpy())
+    rowptr, j, ln, _ = O.rows(geo, hist)
+    return O.csr(rowptr, j, ln, geo.n_vox), rowptr, j, ln, rsp.numpy() * hull.numpy(), hull.numpy()
+
+
+def test_proton_rows_adjoint_identity():
+    # <A x, y> = <x, A^T y> for the oracle's forward and adjoint of proton rows,
+    # and A^T y equals the row-by-row accumulation of y_i a_ij
+    A, rowptr, j, ln, xt, hull = _proton_system(2000)
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0.2, 1.5, A.shape[1])
+    y = rng.normal(size=A.shape[0])
+    ax, aty = O.forward(A, x), O.adjoint(A, y)
+    assert abs(ax @ y - x @ aty) <= 1e-12 * np.abs(ax) @ np.abs(y)
+    acc = np.zeros(A.shape[1])
+    for i in range(A.shape[0]):
+        for e in range(rowptr[i], rowptr[i + 1]):
+            acc[j[e]] += y[i] * ln[e]
+    assert np.allclose(aty, acc, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("lam,block", [(1.0, 4000), (0.5, 400), (1.0, 100), (0.5, 1)])
+def test_drop_residual_falls_monotonically_on_noise_free_proton_data(lam, block):
+    # b = A x_true from the oracle's own rows: every DROP iteration lowers ||A x - b||
+    A, _, _, _, xt, hull = _proton_system()
+    b = A @ xt
+    x = hull.astype(np.float64)
+    res = [np.linalg.norm(A @ x - b)]
+    for _ in range(6):
+        x = O.drop(A, b, 1, lam, block, x)
+        res.append(np.linalg.norm(A @ x - b))
+    assert all(r1 < r0 for r0, r1 in zip(res, res[1:])), res
+    assert res[-1] < 0.5 * res[0]
 
 
 def test_drop_skips_empty_rows_and_untouched_voxels():
