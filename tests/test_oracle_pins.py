@@ -313,6 +313,26 @@ def test_prepare_states_lie_on_the_tracker_lines():
     assert np.min(np.abs(r - np.round(r))) < 1e-9
 
 
+def test_mlp_polyline_starts_and_ends_at_the_hull_states():
+    # the MLP reproduces the measured (hull-projected) entry and exit points:
+    # the first and last vertices of the polyline are those points
+    mask = _ball_mask((30, 30, 10), 9.0)
+    geo = _geo(shape=(30, 30, 10), mask=mask)
+    for phi, th_in, th_out in ((0.7, 0.02, -0.03), (2.2, -0.015, 0.01), (4.0, 0.0, 0.025)):
+        h = _one_proton(phi, t=1.5, v=-0.3, th_in=th_in, ps_in=0.01, th_out=th_out, ps_out=-0.02,
+                        dt=0.8, dv=0.3)
+        st, ok, _ = O.prepare(geo, h)
+        assert ok[0]
+        u_in, u_out, t0, th0, v0, ps0, t2, th2, v2, ps2, c, s = st[0]
+        pts, npts = O.mlp_points(geo, h, 200)
+        p = pts[0, :npts[0]]
+        entry = np.array([u_in * c - t0 * s, u_in * s + t0 * c, v0])
+        exit_ = np.array([u_out * c - t2 * s, u_out * s + t2 * c, v2])
+        assert np.allclose(p[0], entry, rtol=0, atol=1e-12)
+        assert np.allclose(p[-1], exit_, rtol=0, atol=1e-12)
+        assert npts[0] > 3 and np.all(np.isfinite(p))
+
+
 def test_missing_proton_gives_empty_row():
     mask = _ball_mask((20, 20, 6), 5.0)
     geo = _geo(shape=(20, 20, 6), mask=mask)
