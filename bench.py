@@ -697,7 +697,9 @@ def run_batch(args):
         "config": {"workload": "16 scans, protons log-uniform 1e5..2e6 (total %d, %d cross the hull), "
                                "grids 64x64x8..128x128x32, 6 iterations, block 3200, graph-captured "
                                "cooperative launch" % (sum(c.n_protons for c in cfgs), valid),
-                   "cta": c0.stat(pct.PCT_STAT_BATCH_CTA), "ctas": c0.stat(pct.PCT_STAT_BATCH_CTAS)},
+                   "cta": c0.stat(pct.PCT_STAT_BATCH_CTA), "ctas": c0.stat(pct.PCT_STAT_BATCH_CTAS),
+                   "lanes_per_proton": c0.stat(pct.PCT_STAT_BATCH_LANES),
+                   "tuning": "CTA size x lanes per proton autotuned on the first call"},
         "sequential_ms_per_step": ms_s, "speedup_vs_sequential": ms_s / ms_b,
         "max_rel_diff_vs_sequential": worst, "max_abs_diff_vs_sequential": worst_abs,
         "max_abs_diff_sequential_vs_sequential": seq_abs,

@@ -86,8 +86,9 @@ enum pct_option {
      * and replay it while the batch arguments stay the same.  Default 0. */
     PCT_OPT_GRAPH = 6,
     /* pct_solve_batch with this context first: 1 = on the first call with a new
-     * batch, time one iteration with 128- and 256-thread CTAs (on scratch
-     * copies of x) and keep the faster.  Default 0 (use PCT_OPT_CTA_THREADS). */
+     * batch, time one iteration with each of 128- and 256-thread CTAs x 32 and
+     * 16 lanes per proton (on scratch copies of x) and keep the fastest.
+     * Default 0 (use PCT_OPT_CTA_THREADS and PCT_OPT_BATCH_LANES). */
     PCT_OPT_AUTOTUNE = 7,
     /* Polls a batched-solve barrier wait makes before giving up (each poll
      * sleeps ~64 ns); a wait that gives up ends the launch and
@@ -99,7 +100,11 @@ enum pct_option {
     PCT_OPT_TEST_UNREACHABLE_BARRIER = 9,
     /* Chord code of PCT_MODE_PACKED rows (one of enum pct_chord_code).  Default
      * PCT_CHORD_FIXED16.  Changing it drops packed rows. */
-    PCT_OPT_CHORD_CODE = 10
+    PCT_OPT_CHORD_CODE = 10,
+    /* pct_solve_batch with this context first: lanes per proton, 32 (one
+     * proton per warp) or 16 (two per warp), when PCT_OPT_AUTOTUNE is off (the
+     * autotuner picks it with the CTA size).  Default 32. */
+    PCT_OPT_BATCH_LANES = 11
 };
 
 /* Row forms of pct_solve.  The stored forms are built by the same walk as the
@@ -137,7 +142,8 @@ enum pct_stat {
     PCT_STAT_BATCH_CTA = 9,       /* threads per CTA of the last batched solve */
     PCT_STAT_BATCH_CTAS = 10,     /* CTAs of the last batched solve */
     PCT_STAT_GRAPH_REPLAYS = 11,  /* batched solves replayed from a CUDA graph */
-    PCT_STAT_TIMED_LAUNCHES = 12  /* launches of the DROP block kernel timed (PCT_OPT_TIMING) */
+    PCT_STAT_TIMED_LAUNCHES = 12, /* launches of the DROP block kernel timed (PCT_OPT_TIMING) */
+    PCT_STAT_BATCH_LANES = 13     /* lanes per proton of the last batched solve */
 };
 
 /* Create a context on CUDA device `device`.

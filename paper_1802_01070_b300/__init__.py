@@ -31,7 +31,8 @@ PCT_OPT_CTA_THREADS, PCT_OPT_MLP_STEP_UM, PCT_OPT_MEM_CAP_BYTES, PCT_OPT_TIMING,
 PCT_OPT_GRAPH, PCT_OPT_AUTOTUNE, PCT_OPT_SPIN_LIMIT, PCT_OPT_TEST_UNREACHABLE_BARRIER = 6, 7, 8, 9
 PCT_STAT_BATCH_CTA, PCT_STAT_BATCH_CTAS, PCT_STAT_GRAPH_REPLAYS, PCT_STAT_TIMED_LAUNCHES = 9, 10, 11, 12
 PCT_MODE_FUSED, PCT_MODE_CSR, PCT_MODE_PACKED = 0, 1, 2
-PCT_OPT_CHORD_CODE = 10
+PCT_OPT_CHORD_CODE, PCT_OPT_BATCH_LANES = 10, 11
+PCT_STAT_BATCH_LANES = 13
 PCT_CHORD_FIXED16, PCT_CHORD_FP16 = 0, 1
 (PCT_STAT_LAUNCHES, PCT_STAT_FUSED_LAUNCHES, PCT_STAT_FUSED_MS, PCT_STAT_DEVICE_BYTES,
  PCT_STAT_N_PROTONS, PCT_STAT_N_HULL_VOXELS, PCT_STAT_ROW_ENTRIES, PCT_STAT_ROW_BYTES) = 1, 2, 3, 4, 5, 6, 7, 8

@@ -74,7 +74,8 @@ struct pct_ctx {
     // batched solve (pct_solve_batch with this context first)
     int graph = 0, autotune = 0, test_unreachable = 0;
     int64_t spin_limit = 1 << 27;
-    int batch_cta = 0, batch_ctas = 0;
+    int batch_cta = 0, batch_ctas = 0, batch_lanes = 32;
+    int lanes_opt = 32;                  // lanes per proton of batched solves (PCT_OPT_BATCH_LANES)
     int64_t graph_replays = 0;
     ScanDesc* d_scans = nullptr;
     unsigned* d_bar = nullptr;
@@ -90,7 +91,7 @@ struct pct_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<int64_t> graph_key;
     std::vector<std::vector<int64_t>> tuned_keys;
-    std::vector<int> tuned_cta;
+    std::vector<int> tuned_cta, tuned_lanes;
     std::vector<cudaEvent_t> ev;   // pairs (start, stop) of timed fused launches
     size_t ev_used = 0;
     std::string err;
@@ -577,6 +578,10 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
     case PCT_OPT_AUTOTUNE:
         c->autotune = value ? 1 : 0;
         return PCT_OK;
+    case PCT_OPT_BATCH_LANES:
+        if (value != 32 && value != 16) return fail(c, PCT_ERR_ARG, "lanes per proton must be 32 or 16");
+        c->lanes_opt = (int)value;
+        return PCT_OK;
     case PCT_OPT_SPIN_LIMIT:
         if (value < 1 || value > (int64_t)1 << 30) return fail(c, PCT_ERR_ARG, "spin limit must be 1..2^30");
         c->spin_limit = value;
@@ -612,6 +617,7 @@ pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
     case PCT_OPT_CHORD_CODE: *value = c->chord_code; return PCT_OK;
     case PCT_OPT_GRAPH: *value = c->graph; return PCT_OK;
     case PCT_OPT_AUTOTUNE: *value = c->autotune; return PCT_OK;
+    case PCT_OPT_BATCH_LANES: *value = c->lanes_opt; return PCT_OK;
     case PCT_OPT_SPIN_LIMIT: *value = c->spin_limit; return PCT_OK;
     case PCT_OPT_TEST_UNREACHABLE_BARRIER: *value = c->test_unreachable; return PCT_OK;
     default: return PCT_ERR_ARG;
@@ -906,7 +912,7 @@ namespace {
 // Enqueue one batched solve on `stream`: clear barriers and accumulators,
 // prepare every scan's records, launch the persistent kernel.
 pct_status enqueue_batch(pct_ctx* c0, pct_ctx* const* ctxs, int32_t count, const std::vector<ScanDesc>& scans,
-                         int cta, int total, cudaStream_t stream, float* const* x)
+                         int cta, int lanes, int total, cudaStream_t stream, float* const* x)
 {
     int64_t* launches = &c0->launches;
     const Launch L0{stream, c0->cta, launches};
@@ -922,7 +928,7 @@ pct_status enqueue_batch(pct_ctx* c0, pct_ctx* const* ctxs, int32_t count, const
     }
     (void)x;
     if (e == cudaSuccess)
-        e = launch_drop_batch(L0, c0->d_scans, count, total, cta, c0->d_flags, (int)c0->spin_limit,
+        e = launch_drop_batch(L0, c0->d_scans, count, total, cta, lanes, c0->d_flags, (int)c0->spin_limit,
                               c0->test_unreachable);
     return e == cudaSuccess ? PCT_OK : cuda_fail(c0, e, "batched solve");
 }
@@ -981,8 +987,9 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c0->batch_ev[1], cudaEventDisableTiming);
         if (e != cudaSuccess) return cuda_fail(c0, e, "batch stream");
     }
-    // CTA size: autotuned (fastest of 128 / 256 threads on one iteration, on
-    // scratch copies of x), or the context's CTA option
+    // CTA size and lanes per proton: autotuned (fastest of 128 / 256 threads x
+    // 32 / 16 lanes per proton on one iteration, on scratch copies of x), or
+    // the context's options
     // what the tuned CTA size and the captured graph depend on (x pointers and
     // lambda live in the descriptors, uploaded before every launch)
     std::vector<int64_t> key;
@@ -992,11 +999,11 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
         key.push_back(block_size[k]);
         key.push_back(ctxs[k]->n);
     }
-    int cta = c0->cta;
-    auto build_scans = [&](int cta_try, int* total_out, std::vector<ScanDesc>& scans,
+    int cta = c0->cta, lanes = c0->lanes_opt;
+    auto build_scans = [&](int cta_try, int lanes_try, int* total_out, std::vector<ScanDesc>& scans,
                            float* const* xs, const int32_t* its) -> pct_status {
         int cap = 0;
-        cudaError_t e = batch_max_ctas(cta_try, c0->device, &cap);
+        cudaError_t e = batch_max_ctas(cta_try, lanes_try, c0->device, &cap);
         if (e != cudaSuccess) return cuda_fail(c0, e, "batch occupancy");
         if (cap < count) return fail(c0, PCT_ERR_ARG, "more scans than co-resident CTAs");
         scans.assign(count, ScanDesc{});
@@ -1046,6 +1053,7 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
             if (c0->tuned_keys[q] == key) hit = q;
         if (hit < c0->tuned_keys.size()) {
             cta = c0->tuned_cta[hit];
+            lanes = c0->tuned_lanes[hit];
         } else {
             // time each candidate on one iteration over scratch copies of x
             std::vector<float*> tmp(count, nullptr);
@@ -1057,21 +1065,22 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
             }
             std::vector<int32_t> one(count, 1);
             float best = 1e30f;
-            int best_cta = cta;
+            int best_cta = cta, best_lanes = lanes;
             cudaEvent_t t0 = nullptr, t1 = nullptr;
             cudaEventCreate(&t0);
             cudaEventCreate(&t1);
-            for (int cand : {128, 256}) {
+            for (int cand : {128, 256})
+            for (int cand_lanes : {32, 16}) {
                 if (s != PCT_OK) break;
                 std::vector<ScanDesc> scans;
                 int total = 0;
-                if ((s = build_scans(cand, &total, scans, tmp.data(), one.data())) != PCT_OK) break;
+                if ((s = build_scans(cand, cand_lanes, &total, scans, tmp.data(), one.data())) != PCT_OK) break;
                 for (int32_t k = 0; k < count; ++k)
                     cudaMemcpyAsync(tmp[k], x[k], (size_t)ctxs[k]->n_vox * sizeof(float),
                                     cudaMemcpyDeviceToDevice, bs);
                 cudaMemcpyAsync(c0->d_scans, scans.data(), sizeof(ScanDesc) * count, cudaMemcpyHostToDevice, bs);
                 cudaEventRecord(t0, bs);
-                s = enqueue_batch(c0, ctxs, count, scans, cand, total, bs, tmp.data());
+                s = enqueue_batch(c0, ctxs, count, scans, cand, cand_lanes, total, bs, tmp.data());
                 cudaEventRecord(t1, bs);
                 cudaStreamSynchronize(bs);
                 float ms = 0.f;
@@ -1079,6 +1088,7 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
                 if (s == PCT_OK && ms < best) {
                     best = ms;
                     best_cta = cand;
+                    best_lanes = cand_lanes;
                 }
             }
             cudaEventDestroy(t0);
@@ -1086,17 +1096,21 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
             for (float* p : tmp) dfree(c0, p);
             if (s != PCT_OK) return s;
             cta = best_cta;
+            lanes = best_lanes;
             c0->tuned_keys.push_back(key);
             c0->tuned_cta.push_back(cta);
+            c0->tuned_lanes.push_back(lanes);
         }
     }
     key.push_back(cta);
+    key.push_back(lanes);
     std::vector<ScanDesc> scans;
     int total = 0;
-    pct_status s = build_scans(cta, &total, scans, x, iters);
+    pct_status s = build_scans(cta, lanes, &total, scans, x, iters);
     if (s != PCT_OK) return s;
     c0->batch_cta = cta;
     c0->batch_ctas = total;
+    c0->batch_lanes = lanes;
     // descriptors change only with the batch; upload them outside any graph
     e = cudaMemcpyAsync(c0->d_scans, scans.data(), sizeof(ScanDesc) * count, cudaMemcpyHostToDevice, bs);
     if (e == cudaSuccess) e = cudaStreamSynchronize(bs);
@@ -1108,7 +1122,7 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
             cudaGraph_t g = nullptr;
             e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(c0, e, "graph capture");
-            s = enqueue_batch(c0, ctxs, count, scans, cta, total, bs, x);
+            s = enqueue_batch(c0, ctxs, count, scans, cta, lanes, total, bs, x);
             cudaError_t e2 = cudaStreamEndCapture(bs, &g);
             if (s != PCT_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -1128,7 +1142,7 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
         ++c0->graph_replays;
         c0->launches += 1 + count;
     } else {
-        s = enqueue_batch(c0, ctxs, count, scans, cta, total, bs, x);
+        s = enqueue_batch(c0, ctxs, count, scans, cta, lanes, total, bs, x);
         if (s != PCT_OK) return s;
     }
     e = cudaEventRecord(c0->batch_ev[1], bs);
@@ -1190,6 +1204,7 @@ pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
     case PCT_STAT_ROW_BYTES: *value = (double)row_bytes(c); return PCT_OK;
     case PCT_STAT_BATCH_CTA: *value = (double)c->batch_cta; return PCT_OK;
     case PCT_STAT_BATCH_CTAS: *value = (double)c->batch_ctas; return PCT_OK;
+    case PCT_STAT_BATCH_LANES: *value = (double)c->batch_lanes; return PCT_OK;
     case PCT_STAT_GRAPH_REPLAYS: *value = (double)c->graph_replays; return PCT_OK;
     default: return fail(c, PCT_ERR_ARG, "unknown stat key");
     }

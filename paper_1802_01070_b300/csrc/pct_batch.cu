@@ -56,10 +56,13 @@ __device__ __forceinline__ bool scan_barrier(const ScanDesc& d, int* abort_flag,
     return ok != 0;
 }
 
+// G = lanes per proton: 32 (one proton per warp) or 16 (two per warp).
+template <int G>
 __global__ void __launch_bounds__(256, 3)
 k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int spin_limit,
              int test_unreachable)
 {
+    constexpr int kPerWarp = kWarp / G;
     extern __shared__ unsigned char smem[];
     int s = 0;
     while (s + 1 < nscan && (int)blockIdx.x >= scans[s + 1].cta0) ++s;
@@ -77,22 +80,35 @@ k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int
     // only the first barrier of scan 0 is made unreachable by the test option
     int extra = (test_unreachable && s == 0) ? 1 : 0;
     const int lane = threadIdx.x & 31;
+    const int sub = lane / G;   // which proton of the warp's unit this lane's group takes
     for (int it = 0; it < d.iters; ++it) {
         for (int64_t first = 0; first < d.n; first += d.block) {
             const int64_t count = d.block < d.n - first ? d.block : d.n - first;
-            const int per = count >= (int64_t)kBatchGrab * nwarp ? kBatchGrab : 1;
-            const int64_t stat = (int64_t)nwarp * per;   // protons assigned by index
+            const int64_t units = (count + kPerWarp - 1) / kPerWarp;   // kPerWarp protons each
+            const int per = units >= (int64_t)kBatchGrab * nwarp ? kBatchGrab : 1;
+            const int64_t stat = (int64_t)nwarp * per;   // units assigned by index
             int64_t base = (int64_t)warp_in_scan * per, end = base + per;
-            while (base < count) {
-                end = end < count ? end : count;
-                for (int64_t p = base; p < end; ++p) {
+            while (base < units) {
+                end = end < units ? end : units;
+                for (int64_t u = base; u < end; ++u) {
+                    const int64_t p = u * kPerWarp + sub;
                     const int64_t i = first + p;
                     Path P;
-                    if (!load_path(rv, i, d.mc, P)) continue;
+                    if (kPerWarp == 1) {
+                        if (!load_path(rv, i, d.mc, P)) continue;
+                    } else {
+                        // both groups of the warp take part in the walk's shuffles; a
+                        // group without a valid proton walks nothing
+                        __syncwarp();
+                        if (!(p < count && load_path(rv, i, d.mc, P))) {
+                            P = Path{};
+                            P.nseg = 0;
+                        }
+                    }
                     LaneWalk w;
                     float sv, q;
-                    warp_walk<kBatchRunSlots, true, true>(P, d.mc, d.g, d.mask, d.x, flags, slots, d.mc.cmin,
-                                                          w, sv, q);
+                    warp_walk<kBatchRunSlots, true, true, G>(P, d.mc, d.g, d.mask, d.x, flags, slots,
+                                                             d.mc.cmin, w, sv, q);
                     if (!(q > 0.f)) continue;
                     const float r = (rv.get(R_B, i) - sv) / q;
                     float2* acc = d.acc;
@@ -100,7 +116,7 @@ k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int
                         atomicAdd(acc + j, make_float2(l * r, 1.f));
                     });
                 }
-                if (stat >= count) break;
+                if (stat >= units) break;
                 unsigned long long got = 0;
                 if (lane == 0) got = atomicAdd(d.next, (unsigned long long)kBatchGrab);
                 base = stat + (int64_t)__shfl_sync(0xffffffffu, got, 0);
@@ -130,13 +146,22 @@ size_t batch_smem(int cta)
     return (size_t)(cta / kWarp) * kBatchRunSlots * kWarp * 8;
 }
 
-cudaError_t batch_max_ctas(int cta, int device, int* out)
+namespace {
+
+const void* batch_kernel(int lanes)
+{
+    return lanes == 16 ? (const void*)k_drop_batch<16> : (const void*)k_drop_batch<32>;
+}
+
+}  // namespace
+
+cudaError_t batch_max_ctas(int cta, int lanes, int device, int* out)
 {
     int per_sm = 0, sms = 0;
-    cudaError_t e = cudaFuncSetAttribute(k_drop_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)batch_smem(256));
+    const void* k = batch_kernel(lanes);
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(256));
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_drop_batch, cta, batch_smem(cta));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, cta, batch_smem(cta));
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) return e;
@@ -145,7 +170,7 @@ cudaError_t batch_max_ctas(int cta, int device, int* out)
 }
 
 cudaError_t launch_drop_batch(const Launch& L, const ScanDesc* scans_dev, int nscan, int total_ctas,
-                              int cta, unsigned* flags, int spin_limit, int test_unreachable)
+                              int cta, int lanes, unsigned* flags, int spin_limit, int test_unreachable)
 {
     void* args[] = {(void*)&scans_dev, (void*)&nscan, (void*)&flags, (void*)&spin_limit,
                     (void*)&test_unreachable};
@@ -159,7 +184,7 @@ cudaError_t launch_drop_batch(const Launch& L, const ScanDesc* scans_dev, int ns
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelExC(&cfg, (const void*)k_drop_batch, args);
+    cudaError_t e = cudaLaunchKernelExC(&cfg, batch_kernel(lanes), args);
     ++*L.launches;
     return e;
 }

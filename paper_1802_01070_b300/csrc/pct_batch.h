@@ -24,9 +24,10 @@ struct ScanDesc {
     unsigned long long* next;   // work counter of the scan's block steps (zero on entry)
 };
 
+// lanes: lanes per proton, 32 or 16 (two protons per warp)
 size_t batch_smem(int cta);
-cudaError_t batch_max_ctas(int cta, int device, int* out);
+cudaError_t batch_max_ctas(int cta, int lanes, int device, int* out);
 cudaError_t launch_drop_batch(const Launch& L, const ScanDesc* scans_dev, int nscan, int total_ctas,
-                              int cta, unsigned* flags, int spin_limit, int test_unreachable);
+                              int cta, int lanes, unsigned* flags, int spin_limit, int test_unreachable);
 
 }  // namespace pct

@@ -38,16 +38,19 @@ struct RangeEnds {
     float ex, ey, ez;   // point k1
 };
 
+// G: lanes per proton (32, or 16 with two protons per warp); every lane of the
+// warp calls this.
+template <int G = kWarp>
 __device__ __forceinline__ RangeEnds range_ends(const Path& P, const MlpC& mc, const GridC& g,
                                                 int k0, int k1)
 {
     RangeEnds r;
     path_point(P, mc, g, k0, r.ax, r.ay, r.az);   // k0 >= nseg gives the exit point
     const unsigned full = 0xffffffffu;
-    r.ex = __shfl_down_sync(full, r.ax, 1);
-    r.ey = __shfl_down_sync(full, r.ay, 1);
-    r.ez = __shfl_down_sync(full, r.az, 1);
-    if ((threadIdx.x & (kWarp - 1)) == kWarp - 1) path_point(P, mc, g, k1, r.ex, r.ey, r.ez);
+    r.ex = __shfl_down_sync(full, r.ax, 1, G);
+    r.ey = __shfl_down_sync(full, r.ay, 1, G);
+    r.ez = __shfl_down_sync(full, r.az, 1, G);
+    if ((threadIdx.x & (G - 1)) == G - 1) path_point(P, mc, g, k1, r.ex, r.ey, r.ez);
     return r;
 }
 
@@ -207,53 +210,57 @@ struct StoreSink {
     }
 };
 
-// Lane range of a proton with nseg segments.
+// Lane range of a proton with nseg segments (lane of G).
+template <int G = kWarp>
 __device__ __forceinline__ void lane_range(const Path& P, int cmin, int lane, int& k0, int& k1)
 {
-    int C = (P.nseg + kWarp - 1) / kWarp;
+    int C = (P.nseg + G - 1) / G;
     if (C < cmin) C = cmin;
     k0 = lane * C;
     k1 = min(k0 + C, P.nseg);
 }
 
-// Pass 1 for the proton P on the calling warp: walk, store, accumulate, and
-// resolve the runs shared by neighbouring lanes.  Returns the warp-reduced
-// (s, q) on every lane.
-template <int RL, bool DOT, bool CG = false>
+// Pass 1 for the proton P on the calling group of G lanes (the whole warp, or
+// one half of it): walk, store, accumulate, and resolve the runs shared by
+// neighbouring lanes.  Returns the group-reduced (s, q) on every lane of the
+// group.  Every lane of the warp must call it (the shuffles span the warp); a
+// group without a proton passes nseg = 0.  Run slots are indexed by warp lane.
+template <int RL, bool DOT, bool CG = false, int G = kWarp>
 __device__ __forceinline__ void warp_walk(const Path& P, const MlpC& mc, const GridC& g,
                                           const uint8_t* __restrict__ mask,
                                           const float* __restrict__ x, unsigned* flags,
                                           RunSlots slots, int cmin, LaneWalk& w, float& s_all,
                                           float& q_all)
 {
-    const int lane = threadIdx.x & (kWarp - 1);
-    lane_range(P, cmin, lane, w.k0, w.k1);
+    const int wl = threadIdx.x & (kWarp - 1);
+    const int lane = threadIdx.x & (G - 1);
+    lane_range<G>(P, cmin, lane, w.k0, w.k1);
     w.n = 0;
     w.any = false;
     w.head_j = w.tail_j = -1;
     w.head_l = w.tail_l = 0.f;
     w.head_in = w.tail_in = false;
     w.s = w.q = 0.f;
-    w.ends = range_ends(P, mc, g, w.k0, w.k1);
+    w.ends = range_ends<G>(P, mc, g, w.k0, w.k1);
     if (w.k0 < w.k1) {
-        StoreSink<RL, DOT, CG> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, lane, &w, -1, 0.f, 0.f, 0, false};
+        StoreSink<RL, DOT, CG> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, wl, &w, -1, 0.f, 0.f, 0, false};
         walk_points(P, mc, g, flags, w.k0, w.k1, w.ends, sink);
         sink.commit();
     }
     const unsigned full = 0xffffffffu;
-    const int pt_j = __shfl_up_sync(full, w.tail_j, 1);
-    const float pt_l = __shfl_up_sync(full, w.tail_l, 1);
-    const bool p_any = __shfl_up_sync(full, (int)w.any, 1) != 0;
+    const int pt_j = __shfl_up_sync(full, w.tail_j, 1, G);
+    const float pt_l = __shfl_up_sync(full, w.tail_l, 1, G);
+    const bool p_any = __shfl_up_sync(full, (int)w.any, 1, G) != 0;
     w.merged_prev = lane > 0 && p_any && w.any && w.head_j >= 0 && pt_j == w.head_j;
-    w.next_merges = __shfl_down_sync(full, (int)w.merged_prev, 1) != 0 && lane < kWarp - 1;
-    w.next_head_l = __shfl_down_sync(full, w.head_l, 1);
+    w.next_merges = __shfl_down_sync(full, (int)w.merged_prev, 1, G) != 0 && lane < G - 1;
+    w.next_head_l = __shfl_down_sync(full, w.head_l, 1, G);
     float q = w.q;
     if (w.merged_prev && w.head_in) q = fmaf(2.f * pt_l, w.head_l, q);
     float s = w.s;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(full, s, o);
-        q += __shfl_xor_sync(full, q, o);
+    for (int o = G / 2; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(full, s, o, G);
+        q += __shfl_xor_sync(full, q, o, G);
     }
     s_all = s;
     q_all = q;

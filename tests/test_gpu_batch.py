@@ -1,8 +1,9 @@
 """Batched DROP (many scans in one persistent cooperative launch) through the C ABI.
 
 Each scan of the batch must give the result of its own pct_solve (same kernels;
-only the order of FP32 atomics differs); graph capture and replay, and the
-CTA-size autotuner, must not change it; a barrier wait that cannot be met must
+only the order of FP32 atomics differs), with one or two protons per warp;
+graph capture and replay, and the autotuner of CTA size and lanes per proton,
+must not change it; a barrier wait that cannot be met must
 end with PCT_ERR_TIMEOUT, leaving the context usable.
 """
 import numpy as np
@@ -88,11 +89,26 @@ def test_graph_capture_and_replay(scans):
     c0.set_option(pct.PCT_OPT_GRAPH, 0)
 
 
-def test_autotuned_cta_size(scans):
+def test_two_protons_per_warp(scans):
+    # 16 lanes per proton: two protons walk in each warp, with their own shuffles
+    ref = _individual(scans)
+    c0 = scans[0][2]
+    with pytest.raises(pct.PctError) as e:
+        c0.set_option(pct.PCT_OPT_BATCH_LANES, 8)
+    assert e.value.status == pct.PCT_ERR_ARG
+    c0.set_option(pct.PCT_OPT_BATCH_LANES, 16)
+    xs = _batch(scans)
+    assert c0.stat(pct.PCT_STAT_BATCH_LANES) == 16
+    c0.set_option(pct.PCT_OPT_BATCH_LANES, 32)
+    _close(xs, ref, [h for _, h, _ in scans])
+
+
+def test_autotuned_cta_size_and_lanes_per_proton(scans):
     ref = _individual(scans)
     xs = _batch(scans, autotune=True)
     _close(xs, ref, [h for _, h, _ in scans])
     assert scans[0][2].stat(pct.PCT_STAT_BATCH_CTA) in (128, 256)
+    assert scans[0][2].stat(pct.PCT_STAT_BATCH_LANES) in (16, 32)
     scans[0][2].set_option(pct.PCT_OPT_AUTOTUNE, 0)
 
 
