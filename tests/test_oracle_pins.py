@@ -333,6 +333,108 @@ def test_mlp_polyline_starts_and_ends_at_the_hull_states():
         assert npts[0] > 3 and np.all(np.isfinite(p))
 
 
+def _beam_proton(phi, ua, ta, va, ub, tb, vb, th_in, ps_in, th_out, ps_out):
+    """One history given by its tracker points in the beam frame of phi (mm)."""
+    c, s = math.cos(phi), math.sin(phi)
+    return {"in_x": [ua * c - ta * s], "in_y": [ua * s + ta * c], "in_z": [va],
+            "out_x": [ub * c - tb * s], "out_y": [ub * s + tb * c], "out_z": [vb],
+            "theta_in": [th_in], "psi_in": [ps_in], "theta_out": [th_out], "psi_out": [ps_out],
+            "phi": [phi], "wepl": [10.0]}
+
+
+def _beam_coords(p, phi):
+    c, s = math.cos(phi), math.sin(phi)
+    return p[:, 0] * c + p[:, 1] * s, -p[:, 0] * s + p[:, 1] * c, p[:, 2]
+
+
+def _interior_count(L, du, dend):
+    # brute force over candidate sample indices: k >= 1 with k du < L - dend
+    return sum(1 for k in range(1, 100000) if k * du < L - dend)
+
+
+@pytest.mark.parametrize("du", [1.0, 0.7])
+def test_polyline_interior_straight_line_with_angles_and_offsets(du):
+    # Tracker points strictly inside the grid box with every voxel in the hull:
+    # the hull entry and exit are the tracker points themselves.  An exit state
+    # on the straight continuation of the entry state (theta, psi != 0, offsets
+    # != 0, gantry angle != 0) must give a polyline whose interior vertices lie
+    # on that line, at beam depths u_in + k du exactly.  A unit slip between mm
+    # and cm in the sample depth, the path depth or the exit offset bends it.
+    geo = _geo(shape=(60, 60, 20), du=du)
+    th, ps = 0.031, -0.017
+    ua, ta, va, L = -22.3, 4.1, -2.7, 41.37
+    for phi in (0.0, 0.9, 2.4, 5.1):
+        h = _beam_proton(phi, ua, ta, va, ua + L, ta + th * L, va + ps * L, th, ps, th, ps)
+        st, ok, _ = O.prepare(geo, h)
+        assert ok[0] and abs(st[0, 0] - ua) < 1e-12 and abs(st[0, 1] - (ua + L)) < 1e-12
+        pts, npts = O.mlp_points(geo, h, 200)
+        K = _interior_count(L, du, geo.dend)
+        assert npts[0] == K + 2
+        u, t, v = _beam_coords(pts[0, :npts[0]], phi)
+        depths = np.concatenate([[ua], ua + du * np.arange(1, K + 1), [ua + L]])
+        assert np.allclose(u, depths, rtol=0, atol=1e-9)
+        assert np.allclose(t, ta + th * (u - ua), rtol=0, atol=1e-9)
+        assert np.allclose(v, va + ps * (u - ua), rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("L", [10.0, 10.0 - 1e-6, 10.0 + 5e-4, 10.0 + 2e-3, 0.5, 1.0005, 1.0015])
+def test_polyline_sample_count_follows_the_exit_margin(L):
+    # interior samples sit at k du (k >= 1) strictly below L - dend: at
+    # L = 10 + 5e-4 the 10th sample is within dend of the exit and is left out,
+    # at L = 10 + 2e-3 it is kept
+    geo = _geo(shape=(40, 40, 10))
+    ua = -12.0
+    h = _beam_proton(0.4, ua, 1.0, 0.5, ua + L, 1.0, 0.5, 0.0, 0.0, 0.0, 0.0)
+    pts, npts = O.mlp_points(geo, h, 64)
+    K = _interior_count(L, 1.0, 1e-3)
+    assert npts[0] == K + 2
+    u, _, _ = _beam_coords(pts[0, :npts[0]], 0.4)
+    assert np.allclose(u[1:-1], ua + np.arange(1, K + 1), rtol=0, atol=1e-9)
+
+
+def _sigma_quad_cm(ua, ub):
+    """Scattering matrix of depths [ua, ub] (cm) by adaptive quadrature."""
+    f = np.polynomial.Polynomial(O.COEF_200MEV_WATER)
+    pre = E0 ** 2 * (1 + 0.038 * math.log((ub - ua) / X0)) ** 2 / X0
+    m = [si.quad(lambda u, n=n: (ub - u) ** n * f(u), ua, ub, epsabs=0, epsrel=1e-13)[0]
+         for n in (2, 1, 0)]
+    return pre * np.array([[m[0], m[1]], [m[1], m[2]]])
+
+
+def test_polyline_interior_is_the_gaussian_conditional_mean_in_cm():
+    # A curved path: each interior vertex (lab mm) must be the conditional mean
+    # of the scattering model with depths and positions converted to cm here
+    # (the unit of the 1/(beta^2 p^2) fit), conditioned on the hull entry and
+    # exit states.  Computed by adaptive quadrature and textbook Gaussian
+    # conditioning, independently of the oracle's moments.
+    geo = _geo(shape=(80, 80, 24))
+    for phi, (ta, th_in, tb, th_out), (va, ps_in, vb, ps_out) in (
+            (0.6, (3.0, 0.02, -1.5, -0.035), (1.0, -0.01, 2.2, 0.025)),
+            (3.9, (-6.0, -0.04, -2.0, 0.05), (-3.0, 0.03, -4.5, -0.02))):
+        ua, ub = -31.0, 33.5
+        h = _beam_proton(phi, ua, ta, va, ub, tb, vb, th_in, ps_in, th_out, ps_out)
+        pts, npts = O.mlp_points(geo, h, 128)
+        u, t, v = _beam_coords(pts[0, :npts[0]], phi)
+        Lc = (ub - ua) / 10.0
+        worst = 0.0
+        for k in range(1, npts[0] - 1):
+            w = float(k)                      # mm below the entry (du = 1 mm)
+            wc = w / 10.0
+            S1, S2 = _sigma_quad_cm(0.0, wc), _sigma_quad_cm(wc, Lc)
+            R0, R1 = _R(wc), _R(Lc - wc)
+            gain = S1 @ R1.T @ np.linalg.inv(R1 @ S1 @ R1.T + S2)
+            for (p0, a0, p2, a2), got in (((ta, th_in, tb, th_out), t[k]), ((va, ps_in, vb, ps_out), v[k])):
+                y0 = np.array([p0 / 10.0, a0])
+                y2 = np.array([p2 / 10.0, a2])
+                y1 = R0 @ y0 + gain @ (y2 - R1 @ R0 @ y0)
+                worst = max(worst, abs(10.0 * y1[0] - got))
+            assert abs(u[k] - (ua + w)) < 1e-9
+        assert worst < 1e-9, worst
+        # the path is curved: far from the chord between its end points
+        chord = ta + (tb - ta) * (u - ua) / (ub - ua)
+        assert np.max(np.abs(t - chord)) > 0.1
+
+
 def test_missing_proton_gives_empty_row():
     mask = _ball_mask((20, 20, 6), 5.0)
     geo = _geo(shape=(20, 20, 6), mask=mask)
