@@ -404,7 +404,7 @@ def run_ours(args):
                 "issue_note": "the kernel is bound by instruction issue (integer/compare/branch work "
                               "of the voxel walk), not FP32 math: issued warp instructions per SM "
                               "cycle over the 4 the SM can issue, from the committed ncu capture of "
-                              "this kernel source (profiles/drop_fused_torso_block320k.md)",
+                              "this kernel source",
                 "hbm_gbs_algorithmic": hbm_bytes_launch / avg_launch_s / 1e9,
                 "hbm_peak_gbs": peaks.get("hbm_gbs"),
                 "fused_share_of_step": avg_launch_s * 1e3 * fused_n / args.steps / step_ms
@@ -474,29 +474,20 @@ def run_ours(args):
             c2.solve(xg, cfg.iters, cfg.lam, block)
             c2.synchronize()
             xg = xg.cpu().numpy().astype(np.float64)
-        hm = hull_np.astype(bool)
-        structure, chord = diff_voxels(pct, cfg, hull_np, sub, sub_np, local, block)
-        diff = structure | chord
-        rel_all = np.abs(xg - xo) / np.maximum(np.abs(xo), 1e-30)
-        rel = rel_all[hm]
-        clean = hm & ~diff
+        ex = exclusion_voxels(pct, cfg, hull_np, sub, sub_np, local, block)
+        from oracle.compare import solve_parity
+        par = solve_parity(xg, xo, hull_np, ex)
         out["cpu_baseline"] = {"value": vs * cfg.iters / dt, "unit": UNIT, "cores": threads,
                                "kind": "oracle",
                                "sample": "first %d protons (%d cross the hull): rows built once, "
                                          "%d DROP iterations, block %d, FP64, %.1f s"
                                          % (s, vs, cfg.iters, block, dt)}
-        out["rsp_err_vs_fp64"] = {
-            "max_rel_same_structure": float(rel_all[clean].max()),
-            "voxels_structure_differs": int((hm & diff).sum()),
-            "voxels_count_differs": int((hm & structure).sum()),
-            "voxels_chord_differs": int((hm & chord & ~structure).sum()),
-            "max_rel_all": float(rel.max()), "mean_rel_all": float(rel.mean()),
-            "frac_within_1e-3": float((rel <= 1e-3).mean()), "hull_voxels": int(hm.sum()),
-            "sample": "same %d-proton sample, GPU FP32 fused vs oracle FP64; 'same structure' = hull "
-                      "voxels whose DROP count s_j is identical on both sides in every block and "
-                      "whose chords agree within %g mm in every row (a near-face or grazing "
-                      "crossing resolved differently in FP32 and FP64 changes s_j or a chord)"
-                      % (s, CHORD_TOL_MM)}
+        out["rsp_err_vs_fp64"] = dict(
+            par, sample="same %d-proton sample, GPU FP32 %s vs oracle FP64; 'clean' = hull voxels the "
+                        "comparison rule keeps: DROP count s_j identical on both sides in every block, "
+                        "and no near-face row (oracle margin < 1e-4 mm) crossing the voxel with chords "
+                        "that differ by more than 2e-3 mm + 1e-5 mm x the row's crossing conditioning"
+                        % (s, args.mode))
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -505,66 +496,27 @@ def run_ours(args):
     return 0
 
 
-CHORD_TOL_MM = 2e-3   # chords differing by more are a grazing crossing resolved differently
-
-
-def diff_voxels(pct, cfg, hull_np, sub, sub_np, local, block):
-    """Hull voxels where the GPU and oracle rows of a history sample differ in
-    structure: the DROP count s_j of some block differs (a chord one side
-    resolves as zero), or a row crosses the voxel with a chord that FP32 and
-    FP64 resolve more than CHORD_TOL_MM apart (grazing crossing), or the row's
-    voxel sequence differs (near-face row).  Returns (structure, chord) masks."""
-    import numpy as np
-    import torch
-
+def exclusion_voxels(pct, cfg, hull_np, sub, sub_np, local, block):
+    """The voxels the comparison rule leaves out for a history sample: the
+    oracle's rows (with margins and crossing conditioning) against the GPU's
+    rows of the same protons, block by block."""
     import oracle as O
+    from oracle.compare import Exclusion
     geo = O.Geometry(cfg.shape, (cfg.voxel,) * 3, cfg.origin, mask=hull_np)
-    rowptr, jo, lo, _ = O.rows(geo, sub_np)
+    rowptr, jo, lo, margin, cond = O.rows(geo, sub_np, with_cond=True)
     n = int(sub["wepl"].numel())
-    nv = cfg.n_vox
-    nb = (n + block - 1) // block
-    cg = np.zeros(nb * nv, dtype=np.int64)
-    chord = np.zeros(nv, dtype=bool)
-    W = 1024
-    cols = np.arange(W)
+    ex = Exclusion(cfg.n_vox, block)
     with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=local) as c:
         c.load_histories(sub)
         for a in range(0, n, 8192):
             k = min(n, a + 8192) - a
+            _, _, nnz = c.rows(a, k, max_nnz=0)
+            W = max(int(nnz.max().item()), 1)
             idx, ln, nnz = c.rows(a, k, max_nnz=W)
-            idx, ln, nnz = idx.cpu().numpy(), ln.cpu().numpy().astype(np.float64), nnz.cpu().numpy()
-            ng = np.minimum(nnz, W)
-            keep = cols[None, :] < ng[:, None]
-            rows = np.repeat(np.arange(a, a + k)[:, None] // block, W, axis=1)
-            cg += np.bincount(rows[keep].astype(np.int64) * nv + idx[keep], minlength=nb * nv)
-            ro = rowptr[a:a + k + 1]
-            no = np.diff(ro)
-            same_n = (no == nnz) & (nnz <= W)
-            pos = np.clip(ro[:-1, None] + cols[None, :], 0, max(jo.size - 1, 0))
-            valid = keep & same_n[:, None]
-            jj = np.where(valid, jo[pos] if jo.size else -1, -1)
-            ll = np.where(valid, lo[pos] if lo.size else 0.0, 0.0)
-            eq = same_n & np.all(~keep | (idx == jj), axis=1)
-            bad = valid & eq[:, None] & (np.abs(ln - ll) > CHORD_TOL_MM)
-            chord[idx[bad]] = True
-            # rows whose voxel sequences differ (near-face rows): the voxels
-            # whose summed chord in the row differs
-            for r in np.nonzero(~eq)[0]:
-                gj, gl = idx[r, :ng[r]], ln[r, :ng[r]]
-                oj, ol = jo[ro[r]:ro[r + 1]], lo[ro[r]:ro[r + 1]]
-                vox = np.union1d(gj, oj)
-                sg = np.zeros(vox.size)
-                so = np.zeros(vox.size)
-                np.add.at(sg, np.searchsorted(vox, gj), gl)
-                np.add.at(so, np.searchsorted(vox, oj), ol)
-                chord[vox[np.abs(sg - so) > CHORD_TOL_MM]] = True
-    m = rowptr.size - 1
-    rws = np.repeat(np.arange(m), np.diff(rowptr))
-    key = np.unique(rws.astype(np.int64) * nv + jo)
-    blk = (key // nv) // block
-    co = np.bincount(blk * nv + key % nv, minlength=nb * nv)
-    structure = (cg.reshape(nb, nv) != co.reshape(nb, nv)).any(axis=0)
-    return structure, chord
+            e0, e1 = int(rowptr[a]), int(rowptr[a + k])
+            ex.add(a, idx.cpu().numpy(), ln.cpu().numpy(), nnz.cpu().numpy(), rowptr[a:a + k + 1] - e0,
+                   jo[e0:e1], lo[e0:e1], margin[a:a + k], cond[a:a + k])
+    return ex.finish()
 
 
 def run_adam(args):

@@ -146,7 +146,8 @@ enum pct_stat {
     PCT_STAT_BATCH_LANES = 13     /* lanes per proton of the last batched solve */
 };
 
-/* Create a context on CUDA device `device`.
+/* Create a context on CUDA device `device`: the reconstruction volume of
+ * Sec. I, x of A x = b, one RSP value per voxel of `grid`.
  *   grid       -- host pointer, copied.
  *   hull_mask  -- host pointer to nx*ny*nz bytes (nonzero = inside the object
  *                 hull), copied; NULL means every voxel is inside.  Rows only
@@ -241,10 +242,19 @@ pct_status pct_mlp(pct_ctx *ctx, int64_t first, int64_t count, int32_t max_pts, 
 pct_status pct_rows(pct_ctx *ctx, int64_t first, int64_t count, int32_t max_nnz, int32_t *out_idx,
                     float *out_len, int32_t *out_nnz);
 
-/* y = A x (device x: n voxels; device y: m = protons loaded, overwritten). */
+/* y = A x, the projection of Sec. I: y_i = sum_j a_ij x_j over the row of
+ * proton i (its MLP path data), i.e. the WEPL the volume x predicts for it.
+ *   x -- device, n float32 (nx*ny*nz voxels); y -- device, m = protons loaded,
+ *        overwritten (0 for rows that miss the hull).
+ * Enqueued on the context stream.  Errors: PCT_ERR_ARG (null x or y with
+ * protons loaded), PCT_ERR_STATE (no histories), PCT_ERR_CUDA. */
 pct_status pct_forward(pct_ctx *ctx, const float *x, float *y);
 
-/* g = A^T y (device y: m values; device g: n voxels, overwritten). */
+/* g = A^T y, the back projection along the same rows (Sec. I):
+ * g_j = sum_i a_ij y_i; the adjoint of pct_forward (<A x, y> = <x, A^T y>).
+ *   y -- device, m float32; g -- device, n float32, overwritten.
+ * Enqueued on the context stream.  Errors: PCT_ERR_ARG (null g, or null y
+ * with protons loaded), PCT_ERR_STATE, PCT_ERR_CUDA. */
 pct_status pct_adjoint(pct_ctx *ctx, const float *y, float *g);
 
 /* DROP reconstruction (Sec. IV-B): `iters` passes over the protons in blocks
@@ -314,6 +324,15 @@ pct_status pct_synchronize(pct_ctx *ctx);
 pct_status pct_get_stat(pct_ctx *ctx, int32_t key, double *value);
 pct_status pct_reset_stats(pct_ctx *ctx);
 
+/* Diagnostic: out[i] = the FP64 tangent the record kernel applies to tracker
+ * angles (Sec. I: straight tracker lines of slope tan(theta) up to the hull),
+ * for n angles t (rad).  For |t| <= 0.25 it is the Maclaurin series of tan
+ * summed to 11 terms (relative error <= 2.2e-16 there); beyond, the CUDA
+ * library tan.  t, out: device, n doubles.  stream: a cudaStream_t or NULL
+ * (default stream); the call synchronizes it.
+ * Errors: PCT_ERR_ARG (n < 0, null pointer with n > 0), PCT_ERR_CUDA. */
+pct_status pct_tan_angle(const double *t, double *out, int64_t n, void *cuda_stream);
+
 /* ---- DROP reconstruction without device allocation --------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot call cudaMalloc: for example an application that hands all device
@@ -344,9 +363,11 @@ pct_status pct_reset_stats(pct_ctx *ctx);
  * any stream capture.  Every call on a device shares the same arrays and
  * clears the parts that must start at zero itself; calls that overlap on the
  * GPU (from several host threads or streams) race on them.  The call returns
- * after the work has finished.  It allocates and frees no device memory.
- * Errors (status only; pct_last_error does not cover this call): PCT_ERR_ARG,
- * PCT_ERR_CUDA, PCT_ERR_DEVICE. */
+ * after the work has finished: it synchronizes the stream and copies the
+ * device status word back to the host.  It allocates and frees no device
+ * memory.  Errors (status only; pct_last_error does not cover this call):
+ * PCT_ERR_ARG, PCT_ERR_CUDA (every CUDA failure, a launch short of resources
+ * included; never PCT_ERR_OOM), PCT_ERR_DEVICE. */
 #define PCT_NOALLOC_MAX_PROTONS 65536
 #define PCT_NOALLOC_MAX_VOXELS 1048576
 #define PCT_NOALLOC_MAX_SAMPLES 4096

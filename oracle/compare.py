@@ -1,0 +1,180 @@
+"""GPU rows and reconstructions against the FP64 oracle -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use this module.  It holds no reconstruction arithmetic: it
+compares rows and volumes that the GPU path and the oracle produced
+independently, and states the one rule by which a voxel is left out of an RSP
+comparison.
+
+Why voxels are left out at all: the GPU path computes paths in FP32 (positions
+good to ~1e-5 mm), the oracle in FP64.  Where a crossing lies within 1e-4 mm of
+a voxel face (the oracle reports each row's smallest such distance, its
+``margin``), the two may resolve the crossing into different voxels, and DROP's
+count s_j of a block (rows with a_ij > 0, Sec. IV-B) or a chord then differs.
+A voxel whose DROP inputs differ cannot be expected to match.
+
+The rule (one rule, for every test and the benchmark):
+  (a) count: s_j differs between the GPU rows (every visit counts, as the GPU
+      scatter does) and the oracle's rows (one count per row and voxel) in
+      some DROP block;
+  (b) chord: a row that the oracle flags (margin < NEAR_FACE_MM) crosses voxel
+      j with chords that differ by more than chord_tol(cond) on the two sides
+      (for a row whose voxel sequence differs: the row's summed chord in j).
+A row the oracle does not flag must have the same voxel sequence and every
+chord within chord_tol(cond); any other row is counted as ``unexcused`` (a real
+disagreement, which the tests assert away).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+NEAR_FACE_MM = 1e-4     # crossings this close to a voxel face may legitimately differ
+MLP_TOL_MM = 1e-3       # MLP point tolerance
+CHORD_TOL_MM = 2e-3     # chord tolerance (difference of two MLP-derived crossings)
+POS_ERR_MM = 1e-5       # sideways position error of the FP32 path (MLP points agree to ~6e-6 mm)
+
+
+def chord_tol(cond):
+    """Chord tolerance of a row: CHORD_TOL_MM plus POS_ERR_MM times the row's
+    crossing conditioning (a crossing nearly parallel to its face moves along
+    the path by the sideways error over the sine of the angle)."""
+    return CHORD_TOL_MM + POS_ERR_MM * np.asarray(cond, dtype=np.float64)
+
+
+def compare_row_chunk(gidx, glen, gnnz, rowptr, j, ln, margin, cond):
+    """Compare padded GPU rows (m x W) with the oracle's CSR rows of the same protons.
+
+    Returns a dict: ``chord_vox`` (voxels excluded by rule (b)), ``unexcused``
+    (indices of rows that disagree without an oracle flag), ``seq_diff`` (rows
+    whose voxel sequence differs), ``worst`` (largest chord difference on rows
+    with the same sequence), ``rows``.
+    """
+    gidx = np.asarray(gidx)
+    glen = np.asarray(glen, dtype=np.float64)
+    gnnz = np.asarray(gnnz).astype(np.int64)
+    m, W = gidx.shape
+    if m and gnnz.max() > W:
+        raise ValueError("a GPU row has %d entries, more than the %d fetched" % (gnnz.max(), W))
+    cols = np.arange(W)
+    no = np.diff(rowptr)
+    k = np.minimum(gnnz, W)
+    keep = cols[None, :] < k[:, None]
+    same_n = (no == gnnz) & (gnnz <= W)
+    base = rowptr[:-1]
+    pos = np.clip(base[:, None] + cols[None, :], 0, max(j.size - 1, 0))
+    valid = keep & same_n[:, None]
+    jj = np.where(valid, j[pos] if j.size else -1, -1)
+    ll = np.where(valid, ln[pos] if ln.size else 0.0, 0.0)
+    eq = same_n & np.all(~keep | (gidx == jj), axis=1)
+    tol = chord_tol(cond)
+    d = np.where(valid & eq[:, None], np.abs(glen - ll), 0.0)
+    over = d > tol[:, None]
+    flagged = np.asarray(margin) < NEAR_FACE_MM
+    unexcused = (over.any(axis=1) | ~eq) & ~flagged
+    vox = [gidx[over & flagged[:, None]]]
+    for r in np.nonzero(~eq & flagged)[0]:
+        gj, gl = gidx[r, :k[r]], glen[r, :k[r]]
+        oj, ol = j[rowptr[r]:rowptr[r + 1]], ln[rowptr[r]:rowptr[r + 1]]
+        u = np.union1d(gj, oj)
+        sg = np.zeros(u.size)
+        so = np.zeros(u.size)
+        np.add.at(sg, np.searchsorted(u, gj), gl)
+        np.add.at(so, np.searchsorted(u, oj), ol)
+        vox.append(u[np.abs(sg - so) > tol[r]])
+    return {"chord_vox": np.concatenate(vox).astype(np.int64), "unexcused": np.nonzero(unexcused)[0],
+            "seq_diff": int((~eq).sum()), "worst": float(d.max()) if d.size else 0.0, "rows": m}
+
+
+class Exclusion:
+    """Voxels excluded from an RSP comparison, accumulated over row chunks.
+
+    Feed consecutive chunks of rows (GPU padded rows and the oracle's CSR rows
+    of the same protons) in proton order with ``add``; chunks may start and end
+    anywhere, DROP blocks of ``block`` rows are closed as they complete.  Call
+    ``finish`` after the last chunk.
+    """
+
+    def __init__(self, n_vox: int, block: int):
+        self.n_vox = int(n_vox)
+        self.block = int(block)
+        self.count = np.zeros(self.n_vox, dtype=bool)
+        self.chord = np.zeros(self.n_vox, dtype=bool)
+        self.unexcused = []
+        self.seq_diff = 0
+        self.rows = 0
+        self.worst = 0.0
+        self._blk = -1
+        self._cg = np.zeros(self.n_vox, dtype=np.int64)
+        self._co = np.zeros(self.n_vox, dtype=np.int64)
+
+    def _close(self):
+        if self._blk >= 0:
+            self.count |= self._cg != self._co
+            self._cg[:] = 0
+            self._co[:] = 0
+
+    def add(self, first_row, gidx, glen, gnnz, rowptr, j, ln, margin, cond):
+        gidx = np.asarray(gidx)
+        gnnz = np.asarray(gnnz).astype(np.int64)
+        m, W = gidx.shape
+        r = compare_row_chunk(gidx, glen, gnnz, rowptr, j, ln, margin, cond)
+        self.chord[r["chord_vox"]] = True
+        self.unexcused.extend((first_row + r["unexcused"]).tolist())
+        self.seq_diff += r["seq_diff"]
+        self.rows += m
+        self.worst = max(self.worst, r["worst"])
+        blk = (first_row + np.arange(m)) // self.block
+        k = np.minimum(gnnz, W)
+        keep = np.arange(W)[None, :] < k[:, None]
+        g_rows = np.broadcast_to(np.arange(m)[:, None], (m, W))[keep]
+        g_j = gidx[keep].astype(np.int64)
+        o_rows = np.repeat(np.arange(m), np.diff(rowptr))
+        key = np.unique(o_rows.astype(np.int64) * self.n_vox + j.astype(np.int64))
+        ko_rows, ko_j = key // self.n_vox, key % self.n_vox
+        for b in np.unique(blk):
+            if b != self._blk:
+                self._close()
+                self._blk = int(b)
+            sel = blk == b
+            rows_b = np.nonzero(sel)[0]
+            lo, hi = rows_b[0], rows_b[-1] + 1
+            gm = (g_rows >= lo) & (g_rows < hi)
+            self._cg += np.bincount(g_j[gm], minlength=self.n_vox)
+            om = (ko_rows >= lo) & (ko_rows < hi)
+            self._co += np.bincount(ko_j[om], minlength=self.n_vox)
+
+    def finish(self):
+        self._close()
+        self._blk = -1
+        return self
+
+    @property
+    def mask(self):
+        return self.count | self.chord
+
+
+def solve_parity(xg, xo, hull, excluded):
+    """RSP agreement over hull voxels: dict with the max relative error on the
+    voxels the rule keeps (``clean_max``), its mean, the number excluded by
+    count and by chord, and the max / fraction within 1e-3 over all hull
+    voxels."""
+    hm = np.asarray(hull).astype(bool)
+    xg = np.asarray(xg, dtype=np.float64)
+    xo = np.asarray(xo, dtype=np.float64)
+    rel = np.abs(xg - xo) / np.maximum(np.abs(xo), 1e-30)
+    ex = excluded.mask if isinstance(excluded, Exclusion) else np.asarray(excluded, dtype=bool)
+    clean = hm & ~ex
+    out = {"clean_max": float(rel[clean].max()) if clean.any() else 0.0,
+           "clean_mean": float(rel[clean].mean()) if clean.any() else 0.0,
+           "excluded": int((hm & ex).sum()),
+           "all_max": float(rel[hm].max()) if hm.any() else 0.0,
+           "all_mean": float(rel[hm].mean()) if hm.any() else 0.0,
+           "frac_within_1e-3": float((rel[hm] <= 1e-3).mean()) if hm.any() else 1.0,
+           "hull_voxels": int(hm.sum())}
+    if isinstance(excluded, Exclusion):
+        out["excluded_count"] = int((hm & excluded.count).sum())
+        out["excluded_chord_only"] = int((hm & excluded.chord & ~excluded.count).sum())
+        out["rows"] = excluded.rows
+        out["rows_seq_diff"] = excluded.seq_diff
+        out["rows_unexcused"] = len(excluded.unexcused)
+    return out

@@ -47,7 +47,7 @@ EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct
            "pct_load_histories", "pct_hull_states", "pct_mlp", "pct_rows", "pct_forward",
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
            "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam",
-           "pct_solve_batch", "pct_hull_distance")
+           "pct_solve_batch", "pct_hull_distance", "pct_tan_angle")
 
 
 class PctError(RuntimeError):
@@ -99,6 +99,7 @@ def load_library(path: str = LIB_PATH):
         "pct_adam": ([P, P, P, P, P, I64, F, F, F, F, I32], ctypes.c_int),
         "pct_solve_noalloc": ([P, P, I64, P, P, P, P, P, P, I32, F, I64, P, ctypes.c_int, P],
                               ctypes.c_int),
+        "pct_tan_angle": ([P, P, I64, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -260,27 +261,49 @@ PCT_NOALLOC_MAX_VOXELS = 1048576
 
 
 def pct_solve_noalloc(shape, voxel, origin, hull_mask, hist, iters, lam, block_size, x,
-                      device=0, stream=None):
+                      device=None, stream=None):
     """DROP reconstruction that allocates no device memory (see include/pct.h).
 
     hull_mask: CUDA uint8 tensor of nx*ny*nz bytes; hist: dict of 12 CUDA float32
     tensors of equal length; x: CUDA float32 tensor (n voxels), updated in place.
-    Returns the C status (0 = PCT_OK) instead of raising, so callers can test limits.
+    Every tensor must be on one device, which the call runs on (``device``, if
+    given, must name it).  Returns the C status (0 = PCT_OK) instead of raising,
+    so callers can test limits.
     """
     import torch
     g = pct_grid(int(shape[0]), int(shape[1]), int(shape[2]), float(voxel[0]), float(voxel[1]),
                  float(voxel[2]), float(origin[0]), float(origin[1]), float(origin[2]))
+    n_vox = int(shape[0]) * int(shape[1]) * int(shape[2])
     cols = [hist[k] for k in HIST_FIELDS]
     n = cols[0].numel()
     ptrs = [_dptr(c, torch.float32, n, k) for k, c in zip(HIST_FIELDS, cols)]
+    xp = _dptr(x, torch.float32, n_vox, "x")
+    mp = _dptr(hull_mask, torch.uint8, n_vox, "hull_mask")
+    dev = x.device.index if x.device.index is not None else torch.cuda.current_device()
+    if device is not None and int(device) != dev:
+        raise ValueError("x is on cuda:%d, device=%d was given" % (dev, int(device)))
+    for name, t in [("hull_mask", hull_mask)] + list(zip(HIST_FIELDS, cols)):
+        if t.device != x.device:
+            raise ValueError("%s is on %s, x on %s" % (name, t.device, x.device))
     A3 = ctypes.c_void_p * 3
     A2 = ctypes.c_void_p * 2
-    h = int(stream.cuda_stream) if stream is not None else int(torch.cuda.current_stream(device).cuda_stream)
+    h = int(stream.cuda_stream) if stream is not None else int(torch.cuda.current_stream(dev).cuda_stream)
     return load_library().pct_solve_noalloc(
-        ctypes.byref(g), _dptr(hull_mask, torch.uint8, what="hull_mask"), int(n), A3(*ptrs[0:3]),
+        ctypes.byref(g), mp, int(n), A3(*ptrs[0:3]),
         A3(*ptrs[3:6]), A2(ptrs[6], ptrs[7]), A2(ptrs[8], ptrs[9]), ptrs[10], ptrs[11], int(iters),
-        float(lam), int(block_size), _dptr(x, torch.float32, what="x"), int(device),
+        float(lam), int(block_size), xp, int(dev),
         ctypes.c_void_p(h) if h else None)
+
+
+def pct_tan_angle(t, out):
+    """out = the record kernel's FP64 tangent of the angles t (CUDA float64 tensors)."""
+    import torch
+    n = t.numel()
+    h = int(torch.cuda.current_stream(t.device).cuda_stream)
+    st = load_library().pct_tan_angle(_dptr(t, torch.float64, what="t"), _dptr(out, torch.float64, n, "out"),
+                                      int(n), ctypes.c_void_p(h) if h else None)
+    if st != PCT_OK:
+        raise PctError(st, "pct_tan_angle")
 
 
 def pct_tv(ctx, x, eps, grad, value):

@@ -16,11 +16,32 @@
 
 using namespace pct;
 
-namespace {
+namespace pct {
 
-// 1/(beta^2 p^2) of a 200 MeV proton in water, polynomial in depth (cm), MeV^-2:
-// the energy-loss fit used with the most-likely-path formalism.
 const double kCoef200[6] = {7.457e-6, 4.548e-7, -5.777e-8, 1.301e-8, -9.228e-10, 2.687e-11};
+
+// Sigma(0, w), w = k du in cm: moments int_0^w (w-u)^n f(u) du of the depth
+// polynomial f, via int_0^w (w-u)^n u^k du = w^(n+k+1) n! k! / (n+k+1)!, times
+// the Highland prefactor E0^2 (1 + 0.038 ln(w/X0))^2 / X0.
+void mlp_sigma_table(double du_mm, int kmax, float4* tab)
+{
+    static const double fact[10] = {1, 1, 2, 6, 24, 120, 720, 5040, 40320, 362880};
+    tab[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 1; k <= kmax; ++k) {
+        const double w = k * du_mm * 0.1;
+        double mom[3] = {0.0, 0.0, 0.0};
+        for (int n = 0; n < 3; ++n)
+            for (int p = 0; p < 6; ++p)
+                mom[n] += kCoef200[p] * std::pow(w, n + p + 1) * fact[n] * fact[p] / fact[n + p + 1];
+        const double lf = 1.0 + 0.038 * std::log(w / (double)kX0);
+        const double pre = (double)kE0 * (double)kE0 * lf * lf / (double)kX0;
+        tab[k] = make_float4((float)(pre * mom[2]), (float)(pre * mom[1]), (float)(pre * mom[0]), 0.f);
+    }
+}
+
+}  // namespace pct
+
+namespace {
 
 thread_local std::string g_create_error;
 
@@ -152,23 +173,6 @@ void dfree(pct_ctx* c, void* p)
     cudaFree(p);
 }
 
-// Sigma(0, w) for the MLP (w in cm): moments int_0^w (w-u)^n f(u) du of the
-// depth polynomial f, via int_0^w (w-u)^n u^k du = w^(n+k+1) n! k! / (n+k+1)!,
-// times the Highland prefactor E0^2 (1 + 0.038 ln(w/X0))^2 / X0.
-void sigma_from_entry(double w, double S[3])
-{
-    static const double fact[10] = {1, 1, 2, 6, 24, 120, 720, 5040, 40320, 362880};
-    double mom[3] = {0.0, 0.0, 0.0};
-    for (int n = 0; n < 3; ++n)
-        for (int k = 0; k < 6; ++k)
-            mom[n] += kCoef200[k] * std::pow(w, n + k + 1) * fact[n] * fact[k] / fact[n + k + 1];
-    const double lf = 1.0 + 0.038 * std::log(w / (double)kX0);
-    const double pre = (double)kE0 * (double)kE0 * lf * lf / (double)kX0;
-    S[0] = pre * mom[2];
-    S[1] = pre * mom[1];
-    S[2] = pre * mom[0];
-}
-
 double step_mm(const pct_ctx* c)
 {
     return c->du_um > 0 ? (double)c->du_um * 1e-3
@@ -184,12 +188,7 @@ pct_status build_sigma_table(pct_ctx* c)
     const int kmax = (int)std::ceil(diag / du) + 3;
     if (kmax > (1 << 22)) return fail(c, PCT_ERR_ARG, "MLP step too small for this grid");
     std::vector<float4> tab((size_t)kmax + 1);
-    tab[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = 1; k <= kmax; ++k) {
-        double S[3];
-        sigma_from_entry(k * du * 0.1, S);
-        tab[k] = make_float4((float)S[0], (float)S[1], (float)S[2], 0.f);
-    }
+    mlp_sigma_table(du, kmax, tab.data());
     void* p = nullptr;
     pct_status s = dalloc(c, &p, tab.size() * sizeof(float4), "MLP table");
     if (s != PCT_OK) return s;
@@ -1208,6 +1207,21 @@ pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
     case PCT_STAT_GRAPH_REPLAYS: *value = (double)c->graph_replays; return PCT_OK;
     default: return fail(c, PCT_ERR_ARG, "unknown stat key");
     }
+}
+
+pct_status pct_tan_angle(const double* t, double* out, int64_t n, void* cuda_stream)
+{
+    if (n < 0 || (n > 0 && (!t || !out))) return PCT_ERR_ARG;
+    if (n == 0) return PCT_OK;
+    int64_t launches = 0;
+    const Launch L{(cudaStream_t)cuda_stream, 256, &launches};
+    cudaError_t e = launch_tan_angle(L, t, out, n);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(L.stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return PCT_ERR_CUDA;
+    }
+    return PCT_OK;
 }
 
 pct_status pct_reset_stats(pct_ctx* c)

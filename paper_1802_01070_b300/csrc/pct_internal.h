@@ -28,12 +28,21 @@ struct Geo {
     unsigned* flags;      // device error word
 };
 
+// 1/(beta^2 p^2) of a 200 MeV proton in water as a polynomial in depth (cm),
+// MeV^-2: the energy-loss fit used with the most-likely-path formalism (host).
+extern const double kCoef200[6];
+// MLP table tab[k] = Sigma(0, k du) (S00, S01, S11, 0) in cm / rad for
+// k = 0..kmax (tab[0] = 0), evaluated in FP64 on the host.
+void mlp_sigma_table(double du_mm, int kmax, float4* tab);
+
 // dist = chessboard distance of each voxel to the nearest hull voxel (capped at
 // 255); tmp is scratch of the same size.
 cudaError_t launch_hull_dist(const Launch& L, const uint8_t* mask, int nx, int ny, int nz, uint8_t* tmp,
                              uint8_t* dist);
 cudaError_t launch_prepare(const Launch& L, const Geo& G, const float* hist, int64_t stride,
                            int64_t n, float* rec);
+// out[i] = the record kernel's tangent of the angle t[i] (diagnostic)
+cudaError_t launch_tan_angle(const Launch& L, const double* t, double* out, int64_t n);
 // records of protons [first, first + count) only
 cudaError_t launch_prepare_range(const Launch& L, const Geo& G, const float* hist, int64_t stride,
                                  int64_t first, int64_t count, float* rec);

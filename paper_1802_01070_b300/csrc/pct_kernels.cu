@@ -61,6 +61,12 @@ __device__ __forceinline__ double tan_angle(double t)
     return a * t;
 }
 
+__global__ void k_tan_angle(const double* __restrict__ t, double* __restrict__ out, int64_t n)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = tan_angle(t[i]);
+}
+
 __global__ void __launch_bounds__(kMaxCta)
 k_prepare(GridC g, const uint8_t* __restrict__ mask, const uint8_t* __restrict__ dist, unsigned* flags,
           const float* __restrict__ h,
@@ -404,6 +410,13 @@ cudaError_t launch_prepare_range(const Launch& L, const Geo& G, const float* his
     const float Lmax = fminf(diag * 1.0001f + 1e-3f, (float)(G.mc.kmax - 2) * G.mc.du_mm);
     k_prepare<<<grid_for(count, L.cta), L.cta, 0, L.stream>>>(G.g, G.mask, G.dist, G.flags, hist, stride,
                                                               first, count, rec, Lmax);
+    PCT_LAUNCH_TAIL(L);
+}
+
+cudaError_t launch_tan_angle(const Launch& L, const double* t, double* out, int64_t n)
+{
+    if (n <= 0) return cudaSuccess;
+    k_tan_angle<<<grid_for(n, 256), 256, 0, L.stream>>>(t, out, n);
     PCT_LAUNCH_TAIL(L);
 }
 

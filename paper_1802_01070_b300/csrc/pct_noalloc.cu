@@ -48,10 +48,6 @@ struct Scratch {
 Scratch g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
-// Same energy-loss fit as the context path: 1/(beta^2 p^2) of a 200 MeV proton
-// in water, polynomial in depth (cm), MeV^-2.
-const double kCoefFit[6] = {7.457e-6, 4.548e-7, -5.777e-8, 1.301e-8, -9.228e-10, 2.687e-11};
-
 // This entry point has no context to hold a message: failures are reported by
 // status alone (the message argument documents the cause in the source).
 pct_status fail(pct_status s, const std::string&)
@@ -59,10 +55,13 @@ pct_status fail(pct_status s, const std::string&)
     return s;
 }
 
+// Every CUDA failure, a launch that lacks resources included, is PCT_ERR_CUDA:
+// this call allocates nothing, so it never reports PCT_ERR_OOM.
 pct_status cuda_fail(cudaError_t e, const char*)
 {
+    (void)e;
     cudaGetLastError();
-    return e == cudaErrorMemoryAllocation ? PCT_ERR_OOM : PCT_ERR_CUDA;
+    return PCT_ERR_CUDA;
 }
 
 // Device addresses of the scratch arrays for `device`, looked up once with the
@@ -91,23 +90,6 @@ pct_status scratch_for(int device, Scratch& out)
     }
     out = s;
     return PCT_OK;
-}
-
-// Sigma(0, w) table of the MLP, as in the context path (w = k du, cm).
-void sigma_table(double du_mm, int kmax, float4* tab)
-{
-    static const double fact[10] = {1, 1, 2, 6, 24, 120, 720, 5040, 40320, 362880};
-    tab[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int k = 1; k <= kmax; ++k) {
-        const double w = k * du_mm * 0.1;
-        double mom[3] = {0.0, 0.0, 0.0};
-        for (int n = 0; n < 3; ++n)
-            for (int p = 0; p < 6; ++p)
-                mom[n] += kCoefFit[p] * std::pow(w, n + p + 1) * fact[n] * fact[p] / fact[n + p + 1];
-        const double lf = 1.0 + 0.038 * std::log(w / (double)kX0);
-        const double pre = (double)kE0 * (double)kE0 * lf * lf / (double)kX0;
-        tab[k] = make_float4((float)(pre * mom[2]), (float)(pre * mom[1]), (float)(pre * mom[0]), 0.f);
-    }
 }
 
 struct DeviceGuard {
@@ -177,7 +159,7 @@ extern "C" pct_status pct_solve_noalloc(const pct_grid* grid, const uint8_t* hul
     if (st != PCT_OK) return st;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     static thread_local float4 tab[PCT_NOALLOC_MAX_SAMPLES + 1];
-    sigma_table(du, kmax, tab);
+    mlp_sigma_table(du, kmax, tab);
     cudaError_t e = cudaMemcpyAsync(S.sig1, tab, sizeof(float4) * (size_t)(kmax + 1),
                                     cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "MLP table upload");
@@ -200,7 +182,7 @@ extern "C" pct_status pct_solve_noalloc(const pct_grid* grid, const uint8_t* hul
     geo.mc.du_mm = (float)du;
     geo.mc.du_cm = (float)(0.1 * du);
     geo.mc.dend_mm = (float)(1e-3 * du);
-    for (int k = 0; k < 6; ++k) geo.mc.coef[k] = (float)kCoefFit[k];
+    for (int k = 0; k < 6; ++k) geo.mc.coef[k] = (float)kCoef200[k];
     geo.mc.sig1 = S.sig1;
     geo.mc.kmax = kmax;
     const double vdiag = std::sqrt((double)G.dx * G.dx + (double)G.dy * G.dy + (double)G.dz * G.dz);

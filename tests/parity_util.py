@@ -8,11 +8,8 @@ import torch
 
 import oracle as O
 import synth
-
-NEAR_FACE_MM = 1e-4     # crossings this close to a voxel face may legitimately differ (FP32 vs FP64)
-MLP_TOL_MM = 1e-3       # MLP point tolerance
-CHORD_TOL_MM = 2e-3     # chord tolerance (difference of two MLP-derived crossings)
-POS_ERR_MM = 1e-5       # sideways position error of the FP32 path (MLP points agree to ~6e-6 mm)
+from oracle.compare import (CHORD_TOL_MM, MLP_TOL_MM, NEAR_FACE_MM, POS_ERR_MM, Exclusion,  # noqa: F401
+                            chord_tol, solve_parity)
 
 
 @functools.lru_cache(maxsize=8)
@@ -85,63 +82,19 @@ def compare_rows(gidx, glen, gnnz, rowptr, j, ln, margin, cond=None, dL=None,
     return n, excused, worst, bad
 
 
-def structure_diff_voxels(gidx, gnnz, rowptr_o, j_o, block, n_vox):
-    """Voxels whose DROP count s_j differs between the GPU rows and the oracle's
-    rows in at least one block.
-
-    s_j counts the rows of a block with a_ij > 0, so a grazing chord that one
-    side resolves and the other does not (a near-face case) changes s_j by one.
-    gidx/gnnz: GPU rows (visits in path order; the GPU counts each visit, so a
-    near-face return to a voxel counts twice there); rowptr_o/j_o: oracle rows
-    in path order (counted once per row and voxel).
-    """
-    m = gnnz.shape[0]
-    blk_rows = np.arange(m) // block
-    k = np.minimum(gnnz, gidx.shape[1])
-    g_rows = np.repeat(np.arange(m), k)
-    g_j = np.concatenate([gidx[i, :k[i]] for i in range(m)]) if m else np.zeros(0, np.int64)
-    o_rows = np.repeat(np.arange(m), np.diff(rowptr_o))
-    # one count per (row, voxel) on the oracle side, as DROP defines s_j
-    ok = np.unique(o_rows.astype(np.int64) * n_vox + j_o)
-    o_rows_u, o_j_u = ok // n_vox, ok % n_vox
-    nb = int(blk_rows[-1]) + 1 if m else 0
-    co = np.bincount(blk_rows[o_rows_u] * n_vox + o_j_u, minlength=nb * n_vox)
-    # the GPU scatter counts every visit
-    cg = np.bincount(blk_rows[g_rows] * n_vox + g_j.astype(np.int64), minlength=nb * n_vox)
-    diff = (co != cg).reshape(nb, n_vox).any(axis=0) if nb else np.zeros(n_vox, bool)
-    return diff
-
-
-def solve_parity(xg, xo, hull, diff_vox):
-    """(max rel err on hull voxels with identical row structure, count of other
-    hull voxels, max rel err over all hull voxels, fraction within 1e-3)."""
-    hm = hull.astype(bool)
-    rel = np.abs(xg - xo) / np.maximum(np.abs(xo), 1e-30)
-    clean = hm & ~diff_vox
-    return (float(rel[clean].max()) if clean.any() else 0.0, int((hm & diff_vox).sum()),
-            float(rel[hm].max()), float((rel[hm] <= 1e-3).mean()))
-
-
-def chord_diff_voxels(gidx, glen, gnnz, rowptr_o, j_o, ln_o, n_vox, tol=CHORD_TOL_MM):
-    """Voxels crossed by a row whose GPU and oracle chords differ by more than
-    tol (a grazing crossing resolved differently in FP32 and FP64), or by a
-    row whose voxel sequence differs."""
-    m = gnnz.shape[0]
-    out = np.zeros(n_vox, bool)
-    for i in range(m):
-        a, b = rowptr_o[i], rowptr_o[i + 1]
-        k = int(gnnz[i])
-        gj, gl = gidx[i, :k], glen[i, :k]
-        oj, ol = j_o[a:b], ln_o[a:b]
-        if k == oj.size and np.array_equal(gj, oj):
-            bad = np.abs(gl - ol) > tol
-            out[oj[bad]] = True
-        else:
-            # sequences differ (near-face row): flag voxels whose chord sum differs
-            vox = np.union1d(gj, oj)
-            sg = np.zeros(vox.size)
-            so = np.zeros(vox.size)
-            np.add.at(sg, np.searchsorted(vox, gj), gl)
-            np.add.at(so, np.searchsorted(vox, oj), ol)
-            out[vox[np.abs(sg - so) > tol]] = True
-    return out
+def gpu_exclusion(ctx, rowptr, j, ln, margin, cond, block, first=0, count=None, chunk=8192):
+    """The voxels the comparison rule of ``oracle.compare`` leaves out, for the
+    protons [first, first + count) loaded in ``ctx`` against the oracle's CSR
+    rows of the same protons (rowptr indexed from ``first``), DROP blocks of
+    ``block`` rows counted from ``first``."""
+    n = ctx.n - first if count is None else count
+    ex = Exclusion(ctx.n_vox, block)
+    for a in range(0, n, chunk):
+        k = min(n, a + chunk) - a
+        _, _, nnz = ctx.rows(first + a, k, max_nnz=0)
+        W = max(int(nnz.max().item()), 1)
+        gidx, glen, gnnz = ctx.rows(first + a, k, max_nnz=W)
+        e0, e1 = int(rowptr[a]), int(rowptr[a + k])
+        ex.add(a, gidx.cpu().numpy(), glen.cpu().numpy(), gnnz.cpu().numpy(),
+               rowptr[a:a + k + 1] - rowptr[a], j[e0:e1], ln[e0:e1], margin[a:a + k], cond[a:a + k])
+    return ex.finish()

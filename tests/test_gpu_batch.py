@@ -1,17 +1,21 @@
 """Batched DROP (many scans in one persistent cooperative launch) through the C ABI.
 
-Each scan of the batch must give the result of its own pct_solve (same kernels;
-only the order of FP32 atomics differs), with one or two protons per warp;
-graph capture and replay, and the autotuner of CTA size and lanes per proton,
-must not change it; a barrier wait that cannot be met must
-end with PCT_ERR_TIMEOUT, leaving the context usable.
+Each scan of the batch must give the FP64 oracle's DROP result for that scan
+(Sec. IV-B, one DROP per scan; within 1e-3 relative on the voxels the
+comparison rule keeps) and the result of its own pct_solve (same kernels; only
+the order of FP32 atomics differs), with one or two protons per warp; graph
+capture and replay, and the autotuner of CTA size and lanes per proton, must
+not change it; a barrier wait that cannot be met must end with
+PCT_ERR_TIMEOUT, leaving the context usable.
 """
 import numpy as np
 import pytest
 import torch
 
+import oracle as O
 import paper_1802_01070_b300 as pct
 import synth
+from tests import parity_util as U
 
 pytestmark = pytest.mark.gpu
 
@@ -26,9 +30,23 @@ def scans(cuda_device):
         ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull.numpy())
         ctx.load_histories({k: v.cuda() for k, v in hist.items()})
         out.append((cfg, hull.numpy(), ctx))
+        # the scan's own FP64 DROP, and the voxels the comparison rule leaves out
+        hn = synth.to_numpy(hist)
+        geo = U.geometry(cfg, hull.numpy())
+        rowptr, j, ln, margin, cond = O.rows(geo, hn, with_cond=True)
+        A = O.csr(rowptr, j, ln, geo.n_vox)
+        xo = O.drop(A, hn["wepl"].astype(np.float64), cfg.iters, cfg.lam, cfg.block,
+                    hull.numpy().astype(np.float64))
+        ex = U.gpu_exclusion(ctx, rowptr, j, ln, margin, cond, cfg.block)
+        assert not ex.unexcused, ex.unexcused[:10]
+        _ORACLE.append((xo, ex))
     yield out
+    _ORACLE.clear()
     for _, _, ctx in out:
         ctx.close()
+
+
+_ORACLE = []   # per scan: (oracle x after the scan's DROP, Exclusion)
 
 
 def _x0(hull):
@@ -57,6 +75,11 @@ def _close(xs, ref, hulls):
         assert np.array_equal(got[~hm], h.astype(np.float32)[~hm])
     print("batch vs individual solves: max rel diff %.3g" % worst)
     assert worst <= 1e-3
+    # against the FP64 oracle, scan by scan
+    for x, h, (xo, ex) in zip(xs, hulls, _ORACLE):
+        r = U.solve_parity(x.cpu().numpy(), xo, h, ex)
+        print("batch vs oracle: %s" % r)
+        assert r["clean_max"] <= 1e-3 and r["excluded"] <= 0.01 * h.sum()
 
 
 def _batch(scans, graph=False, autotune=False):

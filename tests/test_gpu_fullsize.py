@@ -71,6 +71,32 @@ def _adjoint_identity(ctx, cfg, seed=1):
     assert abs(lhs - rhs) <= 1e-5 * scale, (lhs, rhs, scale)
 
 
+def _oracle_parity(cfg, hull, sub, iters, block, label):
+    """GPU DROP (fused, the benchmark's launch shape) vs the FP64 oracle on the
+    history subset ``sub`` (CUDA tensors): iterations of DROP blocks of
+    ``block`` rows from x0 = 1 inside the hull."""
+    with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull) as c1:
+        c1.load_histories(sub)
+        x = torch.from_numpy(hull.astype(np.float32)).cuda()
+        c1.solve(x, iters, cfg.lam, block)
+        c1.synchronize()
+        xg = x.cpu().numpy().astype(np.float64)
+        sub_np = {k: v.cpu().numpy() for k, v in sub.items()}
+        geo = U.geometry(cfg, hull)
+        rowptr, j, ln, margin, cond = O.rows(geo, sub_np, with_cond=True)
+        ex = U.gpu_exclusion(c1, rowptr, j, ln, margin, cond, block)
+    A = O.csr(rowptr, j, ln, geo.n_vox)
+    del j, ln
+    xo = O.drop(A, sub_np["wepl"].astype(np.float64), iters, cfg.lam, block, hull.astype(np.float64))
+    del A
+    r = U.solve_parity(xg, xo, hull, ex)
+    print("%s: %s" % (label, r))
+    assert r["rows_unexcused"] == 0, ex.unexcused[:10]
+    assert r["clean_max"] <= 1e-3 and r["frac_within_1e-3"] >= 0.999
+    assert r["excluded"] <= 0.01 * hull.sum()
+    return r
+
+
 def test_torso_full_size():
     cfg, rsp, hull, hist, ctx = _full("torso")
     rows, excused, worst = _sampled_rows(cfg, hull, hist, ctx)
@@ -82,26 +108,21 @@ def test_torso_full_size():
     ctx.close()
     del hist
     torch.cuda.empty_cache()
-    with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull) as c1:
-        c1.load_histories(sub)
-        x = torch.from_numpy(hull.astype(np.float32)).cuda()
-        c1.solve(x, 1, cfg.lam, B)
-        c1.synchronize()
-        gidx, glen, gnnz = c1.rows(0, B, max_nnz=1024)
-        gidx, glen, gnnz = gidx.cpu().numpy(), glen.cpu().numpy().astype(np.float64), gnnz.cpu().numpy()
-    sub_np = {k: v.cpu().numpy() for k, v in sub.items()}
-    geo = U.geometry(cfg, hull)
-    rowptr, j, ln, margin = O.rows(geo, sub_np)
-    A = O.csr(rowptr, j, ln, geo.n_vox)
-    xo = O.drop(A, sub_np["wepl"].astype(np.float64), 1, cfg.lam, B, hull.astype(np.float64))
-    # voxels whose DROP count differs, or that a row crosses with a chord that
-    # FP32 and FP64 resolve differently (grazing crossing), are counted apart
-    diff = U.structure_diff_voxels(gidx, gnnz, rowptr, j, B, geo.n_vox)
-    diff |= U.chord_diff_voxels(gidx, glen, gnnz, rowptr, j, ln, geo.n_vox)
-    clean_max, n_diff, all_max, frac = U.solve_parity(x.cpu().numpy().astype(np.float64), xo, hull, diff)
-    print("torso block of %d: clean max rel %.3g, %d structure- or chord-differing voxels, all max "
-          "%.3g, %.5f within 1e-3" % (B, clean_max, n_diff, all_max, frac))
-    assert clean_max <= 1e-3 and frac >= 0.999 and n_diff <= 0.01 * hull.sum()
+    _oracle_parity(cfg, hull, sub, 1, B, "torso, one block of %d, 1 iteration" % B)
+
+
+def test_torso_eight_blocks_six_iterations():
+    # the Gauss-Seidel sequence of DROP blocks (Sec. IV-B, block 320000 as for
+    # the paper's simulated data): the first 8 blocks of the full torso scan,
+    # 6 iterations, every block's update feeding the next
+    cfg = synth.CONFIGS["torso"]
+    rsp, hull = synth.phantom(cfg)
+    hist = synth.histories(cfg, "cuda", chunk=1 << 24, rsp=rsp)
+    B = cfg.block
+    sub = {k: v[:8 * B].clone() for k, v in hist.items()}
+    del hist
+    torch.cuda.empty_cache()
+    _oracle_parity(cfg, hull.numpy(), sub, cfg.iters, B, "torso, 8 blocks of %d, %d iterations" % (B, cfg.iters))
 
 
 def test_head_full_size():

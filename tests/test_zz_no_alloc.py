@@ -55,6 +55,24 @@ def test_noalloc_solve_matches_context_solve_on_two_calls(cuda_device):
         assert np.array_equal(got[~hm], x0.cpu().numpy()[~hm])
 
 
+def test_noalloc_call_takes_no_device_memory(cuda_device):
+    # after a first call (which loads the kernels it uses), a call must leave
+    # the device's free memory exactly as it found it
+    cfg, hull, hist = _scan()
+    dev = cuda_device
+    hd = {k: v.to(dev) for k, v in hist.items()}
+    hull_dev = torch.from_numpy(hull).to(dev)
+    vox = (cfg.voxel,) * 3
+    x = torch.from_numpy(hull.astype(np.float32)).to(dev)
+    assert pct.pct_solve_noalloc(cfg.shape, vox, cfg.origin, hull_dev, hd, 1, LAM, BLOCK, x) == pct.PCT_OK
+    torch.cuda.synchronize(dev)
+    free0, _ = torch.cuda.mem_get_info(dev)
+    assert pct.pct_solve_noalloc(cfg.shape, vox, cfg.origin, hull_dev, hd, ITERS, LAM, BLOCK, x) == pct.PCT_OK
+    torch.cuda.synchronize(dev)
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0, (free0, free1)
+
+
 def test_noalloc_rejects_sizes_beyond_its_limits(cuda_device):
     cfg, hull, hist = _scan()
     dev = cuda_device
@@ -63,7 +81,15 @@ def test_noalloc_rejects_sizes_beyond_its_limits(cuda_device):
     hull_dev = torch.from_numpy(hull).to(dev)
     vox = (cfg.voxel,) * 3
     big = (1024, 1024, 2)                      # 2^21 voxels > the limit
-    assert pct.pct_solve_noalloc(big, vox, cfg.origin, hull_dev, hd, 1, LAM, BLOCK, x) == pct.PCT_ERR_ARG
+    xb = torch.ones(1024 * 1024 * 2, device=dev)
+    hb = torch.ones(1024 * 1024 * 2, dtype=torch.uint8, device=dev)
+    assert pct.pct_solve_noalloc(big, vox, cfg.origin, hb, hd, 1, LAM, BLOCK, xb) == pct.PCT_ERR_ARG
+    assert torch.all(xb == 1.0)
+    # the binding refuses buffers shorter than the grid before calling the library
+    with pytest.raises(ValueError):
+        pct.pct_solve_noalloc(cfg.shape, vox, cfg.origin, hull_dev, hd, 1, LAM, BLOCK, x[:-1])
+    with pytest.raises(ValueError):
+        pct.pct_solve_noalloc(cfg.shape, vox, cfg.origin, hull_dev[:-1], hd, 1, LAM, BLOCK, x)
     many = {k: torch.zeros(pct.PCT_NOALLOC_MAX_PROTONS + 1, device=dev) for k in pct.HIST_FIELDS}
     assert pct.pct_solve_noalloc(cfg.shape, vox, cfg.origin, hull_dev, many, 1, LAM, BLOCK, x) == pct.PCT_ERR_ARG
     x0 = x.clone()
