@@ -169,6 +169,15 @@ def _profiled_traffic(workload):
     return d if per_row else None
 
 
+def measured_ceilings(pct, device, n_slots):
+    """(FP32 TFLOP/s, 1e9 float2 atomics/s) measured now by the library's
+    microbenchmarks on ``device``; the atomic array has the DROP accumulator's
+    size."""
+    tf, _ = pct.pct_peak_fp32(device, repeats=5)
+    ga, _ = pct.pct_peak_atomic(n_slots, device, repeats=5)
+    return tf, ga
+
+
 def _measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -380,8 +389,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel (fused DROP block step)
     peaks = _measured_peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
-    fp32_peak = 148 * 128 * 2 * sm_mhz * 1e6 / 1e12           # TFLOP/s
+    fp32_peak, atomic_peak = measured_ceilings(pct, local, cfg.n_vox)
     avg_launch_s = fused_ms * 1e-3 / max(timed_n, 1)
     blocks_per_iter = math.ceil(n / block)
     flops_launch = fused_flops(valid, mean_pts, mean_nnz) / blocks_per_iter
@@ -394,7 +402,15 @@ def run_ours(args):
                 "traffic": (per_row_traffic * valid / blocks_per_iter) if per_row_traffic else None,
                 "kernel": "k_drop_fused", "avg_launch_ms": avg_launch_s * 1e3,
                 "launches_timed": timed_n, "launches": fused_n,
-                "peak_source": "148 SMs x 128 FP32 lanes x 2 x %g MHz (MEASURED_PEAKS sm_max_mhz)" % sm_mhz,
+                "peak_source": "measured: pct_peak_fp32, FP32 FMA loop filling every SM (best of 5, "
+                               "CUDA events), in this run",
+                "atomic": {"achieved_g_per_s": valid * mean_nnz / blocks_per_iter / avg_launch_s / 1e9,
+                           "peak_g_per_s": atomic_peak,
+                           "frac": valid * mean_nnz / blocks_per_iter / avg_launch_s / 1e9 / atomic_peak,
+                           "peak_source": "measured: pct_peak_atomic, float2 atomicAdd to uniformly "
+                                          "hashed slots of a %d-slot array (the accumulator's size, "
+                                          "L2-resident), in this run" % cfg.n_vox,
+                           "model": "one float2 atomic per visit (%.1f visits per valid row)" % mean_nnz},
                 "flops_model": "(%.1f MLP samples x %d + %.1f segments x %d + %.1f visits x %d) "
                                "per valid row" % (max(mean_pts - 2, 0), FLOP_PER_SAMPLE,
                                                   max(mean_pts - 1, 0), FLOP_PER_SEGMENT, mean_nnz,

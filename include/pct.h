@@ -333,6 +333,28 @@ pct_status pct_reset_stats(pct_ctx *ctx);
  * Errors: PCT_ERR_ARG (n < 0, null pointer with n > 0), PCT_ERR_CUDA. */
 pct_status pct_tan_angle(const double *t, double *out, int64_t n, void *cuda_stream);
 
+/* ---- Roofline ceilings measured on the device -------------------------------
+ * Not part of the paper: the two limits of the fused DROP block step (its MLP
+ * and walk arithmetic, and its scatter), measured so that a reported fraction
+ * of peak has a measured denominator.  Each allocates its own scratch, runs on
+ * the legacy default stream of `device`, synchronizes, and reports the best of
+ * `repeats` timed launches (CUDA events) after one warm-up launch. */
+
+/* FP32 fused multiply-add throughput: every SM filled with threads that each
+ * run 8 independent chains of fmaf.  tflops = 2 x FMAs / best time (TFLOP/s);
+ * best_ms (may be NULL) = that time.  Errors: PCT_ERR_ARG (bad device, null
+ * tflops, repeats < 1), PCT_ERR_CUDA. */
+pct_status pct_peak_fp32(int device, int32_t repeats, double *tflops, double *best_ms);
+
+/* Throughput of float2 atomicAdd (one 8-byte vector atomic, as the DROP
+ * scatter issues per visit) to addresses spread uniformly by a counter-based
+ * hash over an array of n_slots float2 (n_slots * 8 bytes; an array smaller
+ * than L2 measures the L2 atomic units).  gatomics = atomics / best time, in
+ * 1e9 per second.  Errors: PCT_ERR_ARG (bad device, null gatomics, repeats < 1,
+ * n_slots outside 1..2^31), PCT_ERR_CUDA. */
+pct_status pct_peak_atomic(int device, int64_t n_slots, int32_t repeats, double *gatomics,
+                           double *best_ms);
+
 /* ---- DROP reconstruction without device allocation --------------------------
  * The paper has no counterpart to this entry point.  It is for callers that
  * cannot call cudaMalloc: for example an application that hands all device

@@ -47,7 +47,8 @@ EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct
            "pct_load_histories", "pct_hull_states", "pct_mlp", "pct_rows", "pct_forward",
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
            "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam",
-           "pct_solve_batch", "pct_hull_distance", "pct_tan_angle")
+           "pct_solve_batch", "pct_hull_distance", "pct_tan_angle", "pct_peak_fp32",
+           "pct_peak_atomic")
 
 
 class PctError(RuntimeError):
@@ -100,6 +101,8 @@ def load_library(path: str = LIB_PATH):
         "pct_solve_noalloc": ([P, P, I64, P, P, P, P, P, P, I32, F, I64, P, ctypes.c_int, P],
                               ctypes.c_int),
         "pct_tan_angle": ([P, P, I64, P], ctypes.c_int),
+        "pct_peak_fp32": ([ctypes.c_int, I32, P, P], ctypes.c_int),
+        "pct_peak_atomic": ([ctypes.c_int, I64, I32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -304,6 +307,25 @@ def pct_tan_angle(t, out):
                                       int(n), ctypes.c_void_p(h) if h else None)
     if st != PCT_OK:
         raise PctError(st, "pct_tan_angle")
+
+
+def pct_peak_fp32(device=0, repeats=5):
+    """(TFLOP/s, best ms) of the library's FP32 FMA microbenchmark on ``device``."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    st = load_library().pct_peak_fp32(int(device), int(repeats), ctypes.byref(t), ctypes.byref(ms))
+    if st != PCT_OK:
+        raise PctError(st, "pct_peak_fp32")
+    return t.value, ms.value
+
+
+def pct_peak_atomic(n_slots, device=0, repeats=5):
+    """(1e9 float2 atomics/s, best ms) to random slots of an n_slots float2 array."""
+    g, ms = ctypes.c_double(), ctypes.c_double()
+    st = load_library().pct_peak_atomic(int(device), int(n_slots), int(repeats), ctypes.byref(g),
+                                        ctypes.byref(ms))
+    if st != PCT_OK:
+        raise PctError(st, "pct_peak_atomic")
+    return g.value, ms.value
 
 
 def pct_tv(ctx, x, eps, grad, value):
