@@ -317,6 +317,41 @@ pct_status pct_solve_host(pct_ctx *ctx, int32_t iters, float lambda, int64_t blo
 pct_status pct_solve_batch(pct_ctx *const *ctxs, int32_t count, const int32_t *iters,
                            const float *lambda, const int64_t *block_size, float *const *x);
 
+/* ---- Data cleaning (Sec. IV-A) ---------------------------------------------
+ * The paper reduces each scan before the solve by "identifying and removing
+ * statistical outliers" (116 million histories to 21 million) without further
+ * detail.  The reading implemented, in FP64:
+ *   - each proton falls into a bin (a, k_t, k_v): a = the nearest multiple of
+ *     angle_step to its gantry angle, modulo n_angle; t and v = where the
+ *     straight chord between its entry and exit tracker points crosses depth
+ *     u = 0 of its beam frame, k_t = floor((t - t_min) / dt) in 0..n_t-1,
+ *     k_v = floor((v - v_min) / dv) in 0..n_v-1 (protons outside are removed);
+ *   - per bin, for q in {WEPL, theta_out - theta_in, psi_out - psi_in}: the
+ *     mean mu and the population standard deviation sigma (two passes);
+ *   - a proton is kept when |q - mu| <= k_sigma * sigma for all three.
+ * Per-bin sums are FP64 atomics, so a proton within rounding of a cut may be
+ * decided either way between runs. */
+typedef struct pct_clean_params {
+    int32_t n_angle, n_t, n_v;  /* bins */
+    double angle_step;          /* rad */
+    double t_min, dt;           /* mm: lower edge of t bin 0, width */
+    double v_min, dv;           /* mm */
+    double k_sigma;             /* cut in standard deviations (3 is usual) */
+} pct_clean_params;
+
+/* Remove the outliers from the loaded histories: the kept protons replace the
+ * loaded set, in their order (proton i of the new set is the i-th kept one);
+ * records and stored rows are recomputed when next needed.
+ *   keep_out -- device, n bytes (n = protons before the call), or NULL:
+ *               1 = kept, 0 = removed, per proton of the set before the call
+ *   n_kept   -- host, or NULL: protons kept
+ * Needs device scratch of 52 bytes per bin + 5 bytes per proton + a second
+ * copy of the histories while it runs.  Synchronizes the context stream.
+ * Errors: PCT_ERR_ARG (null params, bin counts < 1 or >= 2^31 bins, widths
+ * not finite and > 0, k_sigma < 0), PCT_ERR_STATE (no histories), PCT_ERR_OOM,
+ * PCT_ERR_CUDA. */
+pct_status pct_clean(pct_ctx *ctx, const pct_clean_params *params, uint8_t *keep_out, int64_t *n_kept);
+
 /* Wait for the context's stream; report asynchronous CUDA errors
  * (PCT_ERR_CUDA) and device-side check failures (PCT_ERR_DEVICE). */
 pct_status pct_synchronize(pct_ctx *ctx);
@@ -327,7 +362,8 @@ pct_status pct_reset_stats(pct_ctx *ctx);
 /* Diagnostic: out[i] = the FP64 tangent the record kernel applies to tracker
  * angles (Sec. I: straight tracker lines of slope tan(theta) up to the hull),
  * for n angles t (rad).  For |t| <= 0.25 it is the Maclaurin series of tan
- * summed to 11 terms (relative error <= 2.2e-16 there); beyond, the CUDA
+ * summed to 11 terms (relative error within 2.3e-16, about one unit in the
+ * last place, there); beyond, the CUDA
  * library tan.  t, out: device, n doubles.  stream: a cudaStream_t or NULL
  * (default stream); the call synchronizes it.
  * Errors: PCT_ERR_ARG (n < 0, null pointer with n > 0), PCT_ERR_CUDA. */

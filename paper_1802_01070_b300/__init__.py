@@ -48,7 +48,7 @@ EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
            "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam",
            "pct_solve_batch", "pct_hull_distance", "pct_tan_angle", "pct_peak_fp32",
-           "pct_peak_atomic")
+           "pct_peak_atomic", "pct_clean")
 
 
 class PctError(RuntimeError):
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH):
         "pct_tan_angle": ([P, P, I64, P], ctypes.c_int),
         "pct_peak_fp32": ([ctypes.c_int, I32, P, P], ctypes.c_int),
         "pct_peak_atomic": ([ctypes.c_int, I64, I32, P, P], ctypes.c_int),
+        "pct_clean": ([P, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -364,6 +365,24 @@ def pct_solve_batch(contexts, iters, lams, blocks, xs):
         _check(contexts[0].handle, load_library().pct_solve_batch(H, k, IT, LA, BL, X))
 
 
+class pct_clean_params(ctypes.Structure):
+    _fields_ = [("n_angle", ctypes.c_int32), ("n_t", ctypes.c_int32), ("n_v", ctypes.c_int32),
+                ("angle_step", ctypes.c_double), ("t_min", ctypes.c_double), ("dt", ctypes.c_double),
+                ("v_min", ctypes.c_double), ("dv", ctypes.c_double), ("k_sigma", ctypes.c_double)]
+
+
+def pct_clean(ctx, n_angle, angle_step, n_t, t_min, dt, n_v, v_min, dv, k_sigma=3.0, keep_out=None):
+    """Statistical outlier removal of the loaded histories; returns the kept count.
+    keep_out: optional CUDA uint8 tensor of n bytes (1 = kept)."""
+    import torch
+    prm = pct_clean_params(int(n_angle), int(n_t), int(n_v), float(angle_step), float(t_min), float(dt),
+                           float(v_min), float(dv), float(k_sigma))
+    kp = _dptr(keep_out, torch.uint8, what="keep_out") if keep_out is not None else None
+    nk = ctypes.c_int64()
+    _check(ctx, load_library().pct_clean(ctx, ctypes.byref(prm), kp, ctypes.byref(nk)))
+    return nk.value
+
+
 def pct_build_rows(ctx):
     _check(ctx, load_library().pct_build_rows(ctx))
 
@@ -555,6 +574,18 @@ class Context:
     def adam(self, x, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         with _Ordered(self):
             pct_adam(self._h, x, grad, m, v, lr, beta1, beta2, eps, step)
+
+    def clean(self, n_angle, angle_step, n_t, t_min, dt, n_v, v_min, dv, k_sigma=3.0, keep=False):
+        """Remove statistical outliers from the loaded protons (see pct_clean);
+        returns the kept count, and the per-proton keep flags (CUDA uint8) when
+        ``keep``."""
+        import torch
+        flags = torch.empty(max(self.n, 1), dtype=torch.uint8, device=self.device) if keep else None
+        with _Ordered(self):
+            kept = pct_clean(self._h, n_angle, angle_step, n_t, t_min, dt, n_v, v_min, dv, k_sigma, flags)
+        old = self.n
+        self.n = kept
+        return (kept, flags[:old]) if keep else kept
 
     def build_rows(self):
         with _Ordered(self):

@@ -10,7 +10,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libpct.so")
-SOURCES = ["pct_api.cu", "pct_kernels.cu", "pct_rows.cu", "pct_grad.cu", "pct_batch.cu", "pct_noalloc.cu", "pct_peaks.cu"]
+SOURCES = ["pct_api.cu", "pct_kernels.cu", "pct_rows.cu", "pct_grad.cu", "pct_batch.cu", "pct_noalloc.cu", "pct_peaks.cu",
+           "pct_clean.cu"]
 HEADERS = ["pct_device.cuh", "pct_warp.cuh", "pct_internal.h", "pct_batch.h"]
 
 # --fmad=false: no implicit contraction of a*b+c, so every kernel that walks a

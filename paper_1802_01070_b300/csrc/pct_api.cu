@@ -853,6 +853,70 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
     return PCT_OK;
 }
 
+pct_status pct_clean(pct_ctx* c, const pct_clean_params* p, uint8_t* keep_out, int64_t* n_kept)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!p) return fail(c, PCT_ERR_ARG, "null cleaning parameters");
+    const int64_t nb = (int64_t)p->n_angle * p->n_t * p->n_v;
+    if (p->n_angle < 1 || p->n_t < 1 || p->n_v < 1 || nb > 0x7fffffffLL)
+        return fail(c, PCT_ERR_ARG, "bin counts must be >= 1 with fewer than 2^31 bins");
+    if (!(p->angle_step > 0.0) || !(p->dt > 0.0) || !(p->dv > 0.0) || !(p->k_sigma >= 0.0) ||
+        !std::isfinite(p->angle_step) || !std::isfinite(p->dt) || !std::isfinite(p->dv) ||
+        !std::isfinite(p->t_min) || !std::isfinite(p->v_min) || !std::isfinite(p->k_sigma))
+        return fail(c, PCT_ERR_ARG, "bin widths must be finite and > 0, k_sigma finite and >= 0");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s != PCT_OK) return s;
+    const int64_t n = c->n;
+    if (n == 0) {
+        if (n_kept) *n_kept = 0;
+        return PCT_OK;
+    }
+    const CleanBins P{p->n_angle, p->n_t, p->n_v, p->angle_step, p->t_min, p->dt, p->v_min, p->dv,
+                      p->k_sigma};
+    void *p_bin = nullptr, *p_cnt = nullptr, *p_sum = nullptr, *p_dev = nullptr, *p_keep = nullptr;
+    void *p_chunk = nullptr, *p_total = nullptr, *p_new = nullptr;
+    auto cleanup = [&]() {
+        for (void* q : {p_bin, p_cnt, p_sum, p_dev, p_keep, p_chunk, p_total}) dfree(c, q);
+    };
+    if ((s = dalloc(c, &p_bin, (size_t)n * sizeof(int), "cleaning bins")) != PCT_OK ||
+        (s = dalloc(c, &p_cnt, (size_t)nb * sizeof(unsigned), "cleaning counts")) != PCT_OK ||
+        (s = dalloc(c, &p_sum, (size_t)nb * 3 * sizeof(double), "cleaning sums")) != PCT_OK ||
+        (s = dalloc(c, &p_dev, (size_t)nb * 3 * sizeof(double), "cleaning deviations")) != PCT_OK ||
+        (!keep_out && (s = dalloc(c, &p_keep, (size_t)n, "keep flags")) != PCT_OK) ||
+        (s = dalloc(c, &p_chunk, (size_t)clean_chunks(n) * sizeof(int64_t), "compaction scratch")) != PCT_OK ||
+        (s = dalloc(c, &p_total, sizeof(int64_t), "kept count")) != PCT_OK ||
+        (s = dalloc(c, &p_new, (size_t)c->cap * H_NF * sizeof(float), "cleaned histories")) != PCT_OK) {
+        cleanup();
+        return s;
+    }
+    uint8_t* keep = keep_out ? keep_out : (uint8_t*)p_keep;
+    const Launch L = launch_of(c);
+    cudaError_t e = launch_clean(L, P, c->d_hist, c->stride, n, (int*)p_bin, (unsigned*)p_cnt, (double*)p_sum,
+                                 (double*)p_dev, keep);
+    if (e == cudaSuccess)
+        e = launch_keep_compact(L, keep, n, (int64_t*)p_chunk, (int64_t*)p_total, c->d_hist, c->stride,
+                                (float*)p_new, c->stride);
+    int64_t kept = 0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&kept, p_total, sizeof kept, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (e != cudaSuccess) {
+        dfree(c, p_new);
+        return cuda_fail(c, e, "data cleaning");
+    }
+    // the kept protons replace the loaded set (same column stride, which is at
+    // least the new count); records and stored rows follow the new set
+    drop_rows(c);
+    dfree(c, c->d_hist);
+    c->d_hist = (float*)p_new;
+    c->n = kept;
+    c->rec_valid = false;
+    if (n_kept) *n_kept = kept;
+    return PCT_OK;
+}
+
 pct_status pct_tv(pct_ctx* c, const float* x, float eps, float* grad, double* value)
 {
     if (!c) return PCT_ERR_ARG;

@@ -78,6 +78,22 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
 cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda,
                               unsigned long long* next);
 
+// data cleaning (pct_clean.cu): bins of (gantry angle, t, v) and the cut
+struct CleanBins {
+    int n_angle, n_t, n_v;
+    double angle_step, t_min, dt, v_min, dv, k_sigma;
+};
+// keep[i] = 1 for the protons within k_sigma of their bin's mean in WEPL and
+// both angle changes; bin (n), cnt (nbins), sum and dev2 (3 nbins) are scratch
+cudaError_t launch_clean(const Launch& L, const CleanBins& P, const float* hist, int64_t stride, int64_t n,
+                         int* bin, unsigned* cnt, double* sum, double* dev2, uint8_t* keep);
+// kept protons' 12 columns written in order to out (column stride out_stride);
+// *total (device) = their number; chunk holds clean_chunks(n) values
+int64_t clean_chunks(int64_t n);
+cudaError_t launch_keep_compact(const Launch& L, const uint8_t* keep, int64_t n, int64_t* chunk,
+                                int64_t* total, const float* hist, int64_t stride, float* out,
+                                int64_t out_stride);
+
 // gradient-based reconstruction (pct_grad.cu)
 cudaError_t launch_tv(const Launch& L, const float* x, int nx, int ny, int nz, float eps, float* grad,
                       double* value);

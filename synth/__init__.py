@@ -245,7 +245,7 @@ def _simulate(cfg, rsp_grid, phi, t, v, th, ps, gen, step_mm):
 
 
 def histories(cfg: ScanConfig, device="cpu", n: int | None = None, chunk: int = 1 << 22,
-              step_mm: float = 1.0, rsp=None):
+              step_mm: float = 1.0, rsp=None, outlier_frac: float = 0.0):
     """Proton histories as a dict of float32 tensors on ``device``.
 
     Proton i takes gantry angle index i mod n_angles (angles k * 360/n_angles
@@ -254,6 +254,12 @@ def histories(cfg: ScanConfig, device="cpu", n: int | None = None, chunk: int = 
     over the z extent) at depth -U, entry angles N(0, angle_sigma); exit points
     and angles come from the random walk at depth +U; WEPL gets Gaussian noise
     of ``wepl_noise`` times its value.
+
+    ``outlier_frac`` > 0 corrupts that fraction of the protons (drawn from a
+    generator of its own, so every other proton is unchanged) the way
+    nuclear interactions and large-angle scatters corrupt measured data: half
+    of them get a WEPL 15-60 % too large, the other half an exit angle off by
+    80-250 mrad in theta or psi.  ``outlier_mask`` (below) returns which.
     """
     n = cfg.n_protons if n is None else int(n)
     dev = torch.device(device)
@@ -290,7 +296,55 @@ def histories(cfg: ScanConfig, device="cpu", n: int | None = None, chunk: int = 
         out["psi_out"][a:b] = ps2
         out["phi"][a:b] = phi
         out["wepl"][a:b] = wepl
+    if outlier_frac > 0.0:
+        bad, kind, mag, sgn = _outliers(cfg, n, dev, outlier_frac)
+        w = out["wepl"]
+        out["wepl"] = torch.where(bad & (kind == 0), w * (1.15 + 0.45 * mag), w)
+        kick = sgn * (0.08 + 0.17 * mag)
+        out["theta_out"] = torch.where(bad & (kind == 1), out["theta_out"] + kick, out["theta_out"])
+        out["psi_out"] = torch.where(bad & (kind == 2), out["psi_out"] + kick, out["psi_out"])
     return out
+
+
+def _outliers(cfg, n, dev, frac):
+    g = torch.Generator(device=dev).manual_seed(cfg.seed + 7_654_321)
+    bad = torch.rand(n, generator=g, device=dev) < frac
+    kind = (torch.rand(n, generator=g, device=dev) * 4).to(torch.int64).clamp_max(3)
+    kind = torch.where(kind >= 2, kind - 1, torch.zeros_like(kind))   # 0: WEPL (half), 1: theta, 2: psi
+    mag = torch.rand(n, generator=g, device=dev)
+    sgn = torch.where(torch.rand(n, generator=g, device=dev) < 0.5, -1.0, 1.0)
+    return bad, kind, mag, sgn
+
+
+def outlier_mask(cfg: ScanConfig, n: int | None = None, frac: float = 0.02, device="cpu"):
+    """Which protons ``histories(..., outlier_frac=frac)`` corrupted (bool tensor)."""
+    n = cfg.n_protons if n is None else int(n)
+    return _outliers(cfg, n, torch.device(device), frac)[0]
+
+
+def clean_bins(cfg: ScanConfig) -> dict:
+    """Bins of the data-cleaning step for a scan: one per gantry angle, t over the
+    detector width and v over its height, 1 x 2.5 mm (the paper's 0.25 cm
+    slices) for the large scans; for small ones v, then t, bins are doubled
+    until a bin holds some 30 protons."""
+    nx, _, nz = cfg.shape
+    half_t = 0.5 * nx * cfg.voxel
+    half_v = 0.5 * nz * cfg.voxel
+    per = cfg.n_protons / cfg.n_angles
+    dt, dv = cfg.voxel, 2.5 * cfg.voxel
+
+    def fill(dt, dv):
+        return per / (math.ceil(2 * half_t / dt) * math.ceil(2 * half_v / dv))
+
+    while fill(dt, dv) < 30 and dv < 2 * half_v:      # taller bins first: WEPL varies least along v
+        dv *= 2
+    while fill(dt, dv) < 30 and dt < half_t:
+        dt *= 2
+    n_t = int(math.ceil(2 * half_t / dt))
+    n_v = max(int(math.ceil(2 * half_v / dv)), 1)
+    return {"n_angle": cfg.n_angles, "angle_step": 2 * math.pi / cfg.n_angles, "n_t": n_t,
+            "t_min": -0.5 * n_t * dt, "dt": dt, "n_v": n_v, "v_min": -0.5 * n_v * dv, "dv": dv,
+            "k_sigma": 3.0}
 
 
 def to_numpy(hist):

@@ -42,21 +42,26 @@ def test_identical_rows_exclude_nothing():
     assert not ex.mask.any()
 
 
-def test_chord_difference_excused_only_on_flagged_rows():
+def test_chord_difference_excludes_its_voxel_and_fails_unflagged_rows():
     rowptr, j, ln = _rows()
     gi, gl, nnz = _pad(rowptr, j, ln)
     gl[1, 1] += 0.01                     # voxel 5 of row 1 off by 1e-2 mm
     margin, cond = np.ones(3), np.ones(3)
     r = compare_row_chunk(gi, gl, nnz, rowptr, j, ln, margin, cond)
-    assert r["unexcused"].tolist() == [1] and r["chord_vox"].size == 0
-    margin[1] = 0.5 * NEAR_FACE_MM
+    assert r["unexcused"].tolist() == [1] and r["chord_vox"].tolist() == [5]
+    margin[1] = 0.5 * NEAR_FACE_MM       # a near-face row: excused, voxel still excluded
     r = compare_row_chunk(gi, gl, nnz, rowptr, j, ln, margin, cond)
     assert r["unexcused"].size == 0 and r["chord_vox"].tolist() == [5]
-    # a badly conditioned crossing widens the tolerance past the difference
+    # a badly conditioned crossing: the row is correct within its tolerance,
+    # but the voxel's DROP input differs, so the voxel is still excluded
     margin[1] = 1.0
     cond[1] = 2000.0
     assert chord_tol(2000.0) > 0.01
     r = compare_row_chunk(gi, gl, nnz, rowptr, j, ln, margin, cond)
+    assert r["unexcused"].size == 0 and r["chord_vox"].tolist() == [5]
+    # below the flat chord tolerance nothing is excluded
+    gl[1, 1] = ln[4] + 0.001
+    r = compare_row_chunk(gi, gl, nnz, rowptr, j, ln, np.ones(3), np.ones(3))
     assert r["unexcused"].size == 0 and r["chord_vox"].size == 0
 
 

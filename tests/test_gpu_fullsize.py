@@ -71,30 +71,63 @@ def _adjoint_identity(ctx, cfg, seed=1):
     assert abs(lhs - rhs) <= 1e-5 * scale, (lhs, rhs, scale)
 
 
-def _oracle_parity(cfg, hull, sub, iters, block, label):
+def _oracle_side(cfg, hull, sub_np):
+    geo = U.geometry(cfg, hull)
+    rowptr, j, ln, margin, cond = O.rows(geo, sub_np, with_cond=True)
+    return geo, rowptr, j, ln, margin, cond
+
+
+def _free_running(cfg, hull, sub, iters, block, label, oracle=None):
     """GPU DROP (fused, the benchmark's launch shape) vs the FP64 oracle on the
-    history subset ``sub`` (CUDA tensors): iterations of DROP blocks of
-    ``block`` rows from x0 = 1 inside the hull."""
+    history subset ``sub`` (CUDA tensors): ``iters`` passes over DROP blocks of
+    ``block`` rows from x0 = 1 inside the hull, each side on its own
+    trajectory.  Returns (parity dict, oracle rows)."""
+    sub_np = {k: v.cpu().numpy() for k, v in sub.items()}
+    geo, rowptr, j, ln, margin, cond = oracle or _oracle_side(cfg, hull, sub_np)
     with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull) as c1:
         c1.load_histories(sub)
         x = torch.from_numpy(hull.astype(np.float32)).cuda()
         c1.solve(x, iters, cfg.lam, block)
         c1.synchronize()
         xg = x.cpu().numpy().astype(np.float64)
-        sub_np = {k: v.cpu().numpy() for k, v in sub.items()}
-        geo = U.geometry(cfg, hull)
-        rowptr, j, ln, margin, cond = O.rows(geo, sub_np, with_cond=True)
         ex = U.gpu_exclusion(c1, rowptr, j, ln, margin, cond, block)
     A = O.csr(rowptr, j, ln, geo.n_vox)
-    del j, ln
     xo = O.drop(A, sub_np["wepl"].astype(np.float64), iters, cfg.lam, block, hull.astype(np.float64))
     del A
     r = U.solve_parity(xg, xo, hull, ex)
     print("%s: %s" % (label, r))
     assert r["rows_unexcused"] == 0, ex.unexcused[:10]
-    assert r["clean_max"] <= 1e-3 and r["frac_within_1e-3"] >= 0.999
-    assert r["excluded"] <= 0.01 * hull.sum()
-    return r
+    return r, (geo, rowptr, j, ln, margin, cond)
+
+
+def _teacher_forced(cfg, hull, sub, oracle, block, x_start, label):
+    """Every DROP block step of the GPU's own trajectory from x_start, each
+    compared with the oracle's step from the same x (the GPU's, before the
+    block): the step's arithmetic alone, with no difference carried over from
+    earlier blocks.  Returns the GPU iterate after the pass and the largest
+    relative difference on the voxels the comparison rule keeps."""
+    geo, rowptr, j, ln, margin, cond = oracle
+    sub_np = {k: v.cpu().numpy() for k, v in sub.items()}
+    n = sub["wepl"].numel()
+    x = x_start.clone()
+    worst = 0.0
+    with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull) as ck:
+        for a in range(0, n, block):
+            k = min(n, a + block) - a
+            ck.load_histories({kk: v[a:a + k] for kk, v in sub.items()})
+            xb = x.cpu().numpy().astype(np.float64)
+            ck.solve(x, 1, cfg.lam, block)
+            ck.synchronize()
+            rp = rowptr[a:a + k + 1] - rowptr[a]
+            e0, e1 = int(rowptr[a]), int(rowptr[a + k])
+            ex = U.gpu_exclusion(ck, rp, j[e0:e1], ln[e0:e1], margin[a:a + k], cond[a:a + k], block)
+            A = O.csr(rp, j[e0:e1], ln[e0:e1], geo.n_vox)
+            xo = O.drop(A, sub_np["wepl"][a:a + k].astype(np.float64), 1, cfg.lam, block, xb)
+            r = U.solve_parity(x.cpu().numpy(), xo, hull, ex)
+            assert r["rows_unexcused"] == 0, ex.unexcused[:10]
+            worst = max(worst, r["clean_max"])
+    print("%s: every block step within %.3g relative of the oracle's step" % (label, worst))
+    return x, worst
 
 
 def test_torso_full_size():
@@ -108,21 +141,40 @@ def test_torso_full_size():
     ctx.close()
     del hist
     torch.cuda.empty_cache()
-    _oracle_parity(cfg, hull, sub, 1, B, "torso, one block of %d, 1 iteration" % B)
+    r, _ = _free_running(cfg, hull, sub, 1, B, "torso, one block of %d, 1 iteration" % B)
+    assert r["clean_max"] <= 1e-3 and r["frac_within_1e-3"] >= 0.9999
+    assert r["excluded"] <= 0.01 * hull.sum()
 
 
 def test_torso_eight_blocks_six_iterations():
-    # the Gauss-Seidel sequence of DROP blocks (Sec. IV-B, block 320000 as for
+    # The Gauss-Seidel sequence of DROP blocks (Sec. IV-B, block 320000 as for
     # the paper's simulated data): the first 8 blocks of the full torso scan,
-    # 6 iterations, every block's update feeding the next
+    # 6 iterations.  Teacher-forced, every block step of the first and of the
+    # last iteration matches the oracle's step within 1e-3 on the voxels the
+    # comparison rule keeps.  Free-running, near-face differences (a DROP
+    # count or chord resolved differently in FP32 and FP64) feed later blocks
+    # and spread a little; the bound is on the share of voxels within 1e-3.
     cfg = synth.CONFIGS["torso"]
     rsp, hull = synth.phantom(cfg)
+    hull = hull.numpy()
     hist = synth.histories(cfg, "cuda", chunk=1 << 24, rsp=rsp)
     B = cfg.block
     sub = {k: v[:8 * B].clone() for k, v in hist.items()}
     del hist
     torch.cuda.empty_cache()
-    _oracle_parity(cfg, hull.numpy(), sub, cfg.iters, B, "torso, 8 blocks of %d, %d iterations" % (B, cfg.iters))
+    label = "torso, 8 blocks of %d, %d iterations" % (B, cfg.iters)
+    r, oracle = _free_running(cfg, hull, sub, cfg.iters, B, label + ", free-running")
+    assert r["frac_within_1e-3"] >= 0.999 and r["clean_mean"] <= 1e-4
+    assert r["excluded"] <= 0.01 * hull.sum()
+    x0 = torch.from_numpy(hull.astype(np.float32)).cuda()
+    x1, w1 = _teacher_forced(cfg, hull, sub, oracle, B, x0, label + ", iteration 1 teacher-forced")
+    with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull) as c1:
+        c1.load_histories(sub)
+        x5 = x0.clone()
+        c1.solve(x5, cfg.iters - 1, cfg.lam, B)
+        c1.synchronize()
+    _, w6 = _teacher_forced(cfg, hull, sub, oracle, B, x5, label + ", iteration %d teacher-forced" % cfg.iters)
+    assert w1 <= 1e-3 and w6 <= 1e-3
 
 
 def test_head_full_size():
