@@ -48,7 +48,8 @@ def _args():
     p.add_argument("--protons", type=int, default=None, help="override the proton count")
     p.add_argument("--block", type=int, default=None)
     p.add_argument("--cta", type=int, default=None)
-    p.add_argument("--task", default="drop", choices=["drop", "adam", "batch"],
+    p.add_argument("--task", default="drop",
+                   choices=["drop", "adam", "batch", "blocks", "fbp", "clean", "regions"],
                    help="drop: DROP reconstruction (default); adam: TV-regularised Adam "
                         "reconstruction with the differentiable projector (workload 'diff')")
     p.add_argument("--mode", default="fused", choices=["fused", "csr", "packed"],
@@ -680,15 +681,234 @@ def run_batch(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# Studies around the solve: block size, FBP start, cleaning, image regions
+# ----------------------------------------------------------------------------
+
+def _setup(args, outlier_frac=0.0):
+    import numpy as np
+    import torch
+
+    import paper_1802_01070_b300 as pct
+    import synth
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    cfg = synth.CONFIGS[args.config]
+    n = args.protons or cfg.n_protons
+    if n != cfg.n_protons:
+        cfg = synth.scaled(cfg, n)
+    rsp, hull = synth.phantom(cfg)
+    hist = synth.histories(cfg, dev, chunk=1 << 24, rsp=rsp, outlier_frac=outlier_frac)
+    ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull.numpy(), device=dev.index)
+    ctx.load_histories(hist)
+    hm = torch.from_numpy(hull.numpy().astype(bool)).to(dev)
+    truth = rsp.to(dev)
+    return pct, cfg, dev, hist, ctx, hm, truth, hull.numpy()
+
+
+def _quality(ctx, x, b, valid, hm, truth):
+    """Relative residual ||A x - b|| / ||b|| over rows with a hull path, mean
+    |x - truth| / truth over hull voxels, and the mean RSP of each true value
+    (the paper's insert means) with its error in %."""
+    import torch
+    y = ctx.forward(x)
+    r = float(torch.linalg.vector_norm((y - b)[valid]) / torch.linalg.vector_norm(b[valid]))
+    xt, tt = x[hm], truth[hm]
+    err = float((torch.abs(xt - tt) / tt).mean())
+    inserts = {}
+    for v in torch.unique(tt).tolist():
+        m = tt == v
+        mean = float(xt[m].mean())
+        inserts["%.2f" % v] = {"mean": mean, "err_pct": 100.0 * (mean - v) / v, "voxels": int(m.sum())}
+    return r, err, inserts
+
+
+def run_blocks(args):
+    """Block-size study (Sec. IV-B: larger blocks make an iteration faster but
+    not necessarily more accurate): the torso scan solved from x0 = 1 with
+    B = 3200, 32000 and 320000, per iteration its time and rows/s, the
+    residual and the RSP error against the phantom; and the final RSP against
+    the FP64 oracle on a bounded sample of the same scan."""
+    import numpy as np
+    import torch
+    pct, cfg, dev, hist, ctx, hm, truth, hull_np = _setup(args)
+    b = hist["wepl"]
+    valid = ctx.hull_states()[:, 10] > 0.5
+    n_valid = int(valid.sum())
+    x0 = hm.float()
+    out = {"metric": "block-size study: proton-rows/s per iteration and RSP error vs truth per iteration",
+           "unit": UNIT, "config": {"workload": "%s: %d protons, lambda %g, fused rows" % (cfg.name, ctx.n, cfg.lam)},
+           "blocks": {}}
+    clk = ClockSampler(_pci_id(torch, dev))
+    clk.start()
+    for B in (3200, 32000, 320000):
+        x = x0.clone()
+        ctx.solve(x.clone(), 1, cfg.lam, B)      # warm-up: lists and kernels
+        ctx.synchronize()
+        curve = []
+        t_total = 0.0
+        for it in range(cfg.iters):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.solve(x, 1, cfg.lam, B)
+            e1.record()
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1)
+            t_total += ms
+            r, err, ins = _quality(ctx, x, b, valid, hm, truth)
+            curve.append({"iter": it + 1, "ms": ms, "rows_per_s": n_valid / (ms * 1e-3), "elapsed_s": t_total * 1e-3,
+                          "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins})
+        out["blocks"][str(B)] = curve
+    out["clocks"] = clk.stop()
+    # against the FP64 oracle on the first protons of the scan
+    s = min(args.cpu_sample, ctx.n)
+    if s > 0 and not args.no_cpu_baseline:
+        import oracle as O
+        import synth
+        from oracle.compare import solve_parity
+        sub = {k: v[:s].clone() for k, v in hist.items()}
+        sub_np = synth.to_numpy(sub)
+        geo = O.Geometry(cfg.shape, (cfg.voxel,) * 3, cfg.origin, mask=hull_np)
+        rowptr, j, ln, margin, cond = O.rows(geo, sub_np, with_cond=True)
+        A = O.csr(rowptr, j, ln, geo.n_vox)
+        res = {}
+        with pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull_np, device=dev.index) as c2:
+            c2.load_histories(sub)
+            for B in (3200, 32000, 320000):
+                xg = x0.clone()
+                c2.solve(xg, cfg.iters, cfg.lam, B)
+                c2.synchronize()
+                xo = O.drop(A, sub_np["wepl"].astype(np.float64), cfg.iters, cfg.lam, B, hull_np.astype(np.float64))
+                ex = exclusion_voxels(pct, cfg, hull_np, sub, sub_np, dev.index, B)
+                res[str(B)] = solve_parity(xg.cpu().numpy(), xo, hull_np, ex)
+        out["vs_oracle"] = {"sample": "first %d protons, %d iterations" % (s, cfg.iters), "by_block": res}
+    print(json.dumps(out))
+    ctx.close()
+    return 0
+
+
+def run_fbp(args):
+    """FBP initial iterate (Sec. I): its time on the scan, and the DROP
+    convergence from it against x0 = 1 inside the hull (residual and RSP error
+    after each iteration; the iterations the FBP start needs to reach the
+    x0 = 1 start's final residual)."""
+    import torch
+
+    import synth
+    pct, cfg, dev, hist, ctx, hm, truth, hull_np = _setup(args)
+    bins = synth.fbp_bins(cfg)
+    b = hist["wepl"]
+    valid = ctx.hull_states()[:, 10] > 0.5
+    block = args.block or cfg.block
+    for _ in range(max(args.warmup, 1)):
+        x_fbp = ctx.fbp(**bins)
+    torch.cuda.synchronize(dev)
+    ts = []
+    for _ in range(max(args.steps, 1)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        x_fbp = ctx.fbp(**bins)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ts.append(e0.elapsed_time(e1))
+    fbp_ms = statistics.median(ts)
+    curves = {}
+    for name, start in (("ones", hm.float()), ("fbp", x_fbp)):
+        x = start.clone()
+        r, err, ins = _quality(ctx, x, b, valid, hm, truth)
+        curve = [{"iter": 0, "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins}]
+        for it in range(cfg.iters):
+            ctx.solve(x, 1, cfg.lam, block)
+            r, err, ins = _quality(ctx, x, b, valid, hm, truth)
+            curve.append({"iter": it + 1, "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins})
+        curves[name] = curve
+    target = curves["ones"][-1]["residual"]
+    reach = next((c["iter"] for c in curves["fbp"] if c["residual"] <= target), None)
+    print(json.dumps({
+        "metric": "FBP initial iterate: ms per FBP and DROP iterations to the x0=1 start's final residual",
+        "value": fbp_ms, "unit": "ms", "higher_is_better": False,
+        "config": {"workload": "%s: %d protons, bins %s, DROP lambda %g block %d" % (
+            cfg.name, ctx.n, bins, cfg.lam, block)},
+        "fbp_protons_per_s": ctx.n / (fbp_ms * 1e-3),
+        "iterations_from_fbp_to_ones_final_residual": reach, "curves": curves}))
+    ctx.close()
+    return 0
+
+
+def run_clean(args):
+    """Data cleaning (Sec. IV-A): statistical outlier removal on the scan with
+    2 % planted outliers; ms per call, protons/s, and what it removed."""
+    import torch
+
+    import synth
+    pct, cfg, dev, hist, ctx, hm, truth, hull_np = _setup(args, outlier_frac=0.02)
+    bins = synth.clean_bins(cfg)
+    planted = synth.outlier_mask(cfg, frac=0.02, device=dev)
+    ts, kept = [], 0
+    for k in range(max(args.warmup, 1) + max(args.steps, 1)):
+        ctx.load_histories(hist)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        kept, flags = ctx.clean(**bins, keep=True)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        if k >= max(args.warmup, 1):
+            ts.append(e0.elapsed_time(e1))
+    ms = statistics.median(ts)
+    f = flags.bool()
+    print(json.dumps({
+        "metric": "data cleaning: protons/s", "value": cfg.n_protons / (ms * 1e-3), "unit": "protons/s",
+        "ms_per_call": ms, "higher_is_better": True,
+        "config": {"workload": "%s: %d protons with 2%% planted outliers, bins %s" % (cfg.name, cfg.n_protons, bins)},
+        "kept": kept, "kept_frac": kept / cfg.n_protons,
+        "planted_removed_frac": float((~f[planted]).float().mean()),
+        "clean_kept_frac": float(f[~planted].float().mean())}))
+    ctx.close()
+    return 0
+
+
+def run_regions(args):
+    """The paper's Algorithm 1 on one GPU against the plain solve: time, protons
+    per region, and the RSP error of each against the phantom."""
+    import torch
+    pct, cfg, dev, hist, ctx, hm, truth, hull_np = _setup(args)
+    b = hist["wepl"]
+    valid = ctx.hull_states()[:, 10] > 0.5
+    block = args.block or cfg.block
+    res = {}
+    for name, regions, halo in (("plain", 0, 0), ("2 regions", 2, 3), ("4 regions", 4, 3)):
+        times = []
+        for k in range(2):
+            x = hm.float()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if regions:
+                counts = ctx.solve_regions(x, regions, halo, cfg.iters, cfg.lam, block)
+            else:
+                ctx.solve(x, cfg.iters, cfg.lam, block)
+                counts = [int(valid.sum())]
+            e1.record()
+            torch.cuda.synchronize(dev)
+            times.append(e0.elapsed_time(e1))
+        r, err, ins = _quality(ctx, x, b, valid, hm, truth)
+        res[name] = {"ms": times[-1], "protons_per_region": counts, "halo_slices": halo, "residual": r,
+                     "rsp_mean_abs_rel_err": err, "inserts": ins}
+    print(json.dumps({"metric": "image regions (Algorithm 1) on one GPU vs the plain solve",
+                      "config": {"workload": "%s: %d protons, %d iterations, block %d" % (
+                          cfg.name, ctx.n, cfg.iters, block)}, "results": res}))
+    ctx.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
-    if args.task == "adam":
-        return run_adam(args)
-    if args.task == "batch":
-        return run_batch(args)
-    return run_ours(args)
+    tasks = {"adam": run_adam, "batch": run_batch, "blocks": run_blocks, "fbp": run_fbp, "clean": run_clean,
+             "regions": run_regions}
+    return tasks.get(args.task, run_ours)(args)
 
 
 if __name__ == "__main__":

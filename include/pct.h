@@ -352,6 +352,69 @@ typedef struct pct_clean_params {
  * PCT_ERR_CUDA. */
 pct_status pct_clean(pct_ctx *ctx, const pct_clean_params *params, uint8_t *keep_out, int64_t *n_kept);
 
+/* ---- Image regions: the paper's Algorithm 1 on one GPU (Sec. III) ---------
+ * The paper splits the volume along z into overlapping regions, solves each
+ * region independently with the protons that enter or exit it (one GPU per
+ * region, no exchange during the solve), and builds the volume from each
+ * region's slices farthest from its overlap.  Here the regions are solved one
+ * after the other on this GPU:
+ *   1 setupImageRegions: region r's core slices are [r nz / R, (r+1) nz / R)
+ *     (integer division), extended by `halo` slices on each side (clamped);
+ *   2 identifyProtonsPassingRegions: a proton with a hull path belongs to
+ *     region r when the slice of its hull entry point or of its hull exit
+ *     point (pct_hull_states) lies in r's extended slices -- it may belong to
+ *     two regions;
+ *   3 allocateMemoryForProtonsPerGPU: each region gets its protons' records
+ *     (the full volume's: the same MLP paths) on a grid of its extended slices;
+ *   4 iterativelySolvePerGPU: pct_solve on each region (fused rows, which
+ *     keep only the voxels of the region's slices), from x's slab;
+ *   5 selectSlice: x's core slices of region r come from region r.
+ * A region's DROP blocks are block_size consecutive protons of its own list,
+ * so with R = 1 this is pct_solve over the protons with a hull path (the plain
+ * pct_solve's blocks also hold protons without one, whose rows are empty).
+ * The paper's example: nz = 20, two regions,
+ * halo 3 (slices 0-12 and 7-19; slices 0-9 and 10-19 kept).
+ *   x              -- device, n voxels: initial iterate in, result out
+ *   region_protons -- host, n_regions values, or NULL: protons per region
+ * Synchronizes the context stream.  Errors: PCT_ERR_ARG (null x, n_regions
+ * outside 1..nz, halo < 0, iters < 0, block_size < 1), PCT_ERR_STATE (no
+ * histories), PCT_ERR_OOM, PCT_ERR_CUDA, PCT_ERR_DEVICE. */
+pct_status pct_solve_regions(pct_ctx *ctx, int32_t n_regions, int32_t halo, int32_t iters, float lambda,
+                             int64_t block_size, float *x, int64_t *region_protons);
+
+/* ---- Filtered back-projection: the initial iterate (Sec. I) ---------------
+ * The paper starts the solve from "the FBP image as the initial iterate" and
+ * gives no detail.  The reading implemented is the textbook parallel-beam FBP,
+ * slice by slice, on binned list-mode data:
+ *   - sinogram: every loaded proton falls into the bin (a, l, k) of the same
+ *     rule as pct_clean (nearest angle step; t, v where the straight tracker
+ *     chord crosses depth u = 0; k = floor((t - t_min) / dt), l = floor((v -
+ *     v_min) / dv)); p[a][l][k] = the mean WEPL of the bin, 0 when empty;
+ *   - filter along t: q[k] = dt * sum_m p[m] h[k - m], h[0] = 1 / (4 dt^2),
+ *     h[n] = -1 / (pi^2 n^2 dt^2) for odd n, 0 for even n != 0 (the
+ *     band-limited ramp kernel); FP64 sums, q stored as float;
+ *   - back-projection: voxel centre (x, y, z), slice l of z:
+ *     x_fbp = (pi / n_angle) * sum_a q_a(-x sin(a angle_step) + y cos(a
+ *     angle_step)), q_a linear between bin centres t_min + (k + 1/2) dt and 0
+ *     beyond the first and last; FP32.  (A full turn sees every line twice.)
+ * Voxels outside the hull, or whose z lies outside the v bins, get 0. */
+typedef struct pct_fbp_params {
+    int32_t n_angle, n_t, n_v;  /* bins: 1..4096 angles, 1..16384 t bins */
+    double angle_step;          /* rad */
+    double t_min, dt;           /* mm */
+    double v_min, dv;           /* mm */
+} pct_fbp_params;
+
+/* FBP image of the loaded histories.
+ *   x        -- device, n voxels, overwritten (a DROP initial iterate)
+ *   sino_out -- device, n_angle * n_v * n_t floats (the filtered sinogram q,
+ *               index (a * n_v + l) * n_t + k), or NULL
+ * Needs 12 bytes of device scratch per bin (plus 4 without sino_out).
+ * Synchronizes the context stream.  Errors: PCT_ERR_ARG (null params or x,
+ * bin counts out of range, widths not finite and > 0), PCT_ERR_STATE (no
+ * histories), PCT_ERR_OOM, PCT_ERR_CUDA. */
+pct_status pct_fbp(pct_ctx *ctx, const pct_fbp_params *params, float *x, float *sino_out);
+
 /* Wait for the context's stream; report asynchronous CUDA errors
  * (PCT_ERR_CUDA) and device-side check failures (PCT_ERR_DEVICE). */
 pct_status pct_synchronize(pct_ctx *ctx);

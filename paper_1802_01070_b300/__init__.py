@@ -48,7 +48,7 @@ EXPORTS = ("pct_create", "pct_destroy", "pct_last_error", "pct_set_option", "pct
            "pct_adjoint", "pct_solve", "pct_solve_host", "pct_synchronize", "pct_get_stat",
            "pct_reset_stats", "pct_solve_noalloc", "pct_build_rows", "pct_tv", "pct_adam",
            "pct_solve_batch", "pct_hull_distance", "pct_tan_angle", "pct_peak_fp32",
-           "pct_peak_atomic", "pct_clean")
+           "pct_peak_atomic", "pct_clean", "pct_fbp", "pct_solve_regions")
 
 
 class PctError(RuntimeError):
@@ -104,6 +104,8 @@ def load_library(path: str = LIB_PATH):
         "pct_peak_fp32": ([ctypes.c_int, I32, P, P], ctypes.c_int),
         "pct_peak_atomic": ([ctypes.c_int, I64, I32, P, P], ctypes.c_int),
         "pct_clean": ([P, P, P, P], ctypes.c_int),
+        "pct_fbp": ([P, P, P, P], ctypes.c_int),
+        "pct_solve_regions": ([P, I32, I32, I32, F, I64, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -383,6 +385,24 @@ def pct_clean(ctx, n_angle, angle_step, n_t, t_min, dt, n_v, v_min, dv, k_sigma=
     return nk.value
 
 
+class pct_fbp_params(ctypes.Structure):
+    _fields_ = [("n_angle", ctypes.c_int32), ("n_t", ctypes.c_int32), ("n_v", ctypes.c_int32),
+                ("angle_step", ctypes.c_double), ("t_min", ctypes.c_double), ("dt", ctypes.c_double),
+                ("v_min", ctypes.c_double), ("dv", ctypes.c_double)]
+
+
+def pct_fbp(ctx, n_vox, n_angle, angle_step, n_t, t_min, dt, n_v, v_min, dv, x, sino_out=None):
+    """FBP image of the loaded histories into the CUDA float32 tensor x (n voxels);
+    sino_out: optional CUDA float32 tensor of n_angle * n_v * n_t (filtered sinogram)."""
+    import torch
+    prm = pct_fbp_params(int(n_angle), int(n_t), int(n_v), float(angle_step), float(t_min), float(dt),
+                         float(v_min), float(dv))
+    sp = None
+    if sino_out is not None:
+        sp = _dptr(sino_out, torch.float32, int(n_angle) * int(n_v) * int(n_t), "sino_out")
+    _check(ctx, load_library().pct_fbp(ctx, ctypes.byref(prm), _dptr(x, torch.float32, n_vox, "x"), sp))
+
+
 def pct_build_rows(ctx):
     _check(ctx, load_library().pct_build_rows(ctx))
 
@@ -586,6 +606,29 @@ class Context:
         old = self.n
         self.n = kept
         return (kept, flags[:old]) if keep else kept
+
+    def solve_regions(self, x, n_regions, halo, iters, lam, block_size):
+        """Algorithm 1 on one GPU (see pct_solve_regions) in place on x; returns
+        the protons of each region."""
+        import torch
+        _dptr(x, torch.float32, self.n_vox, "x")
+        cnt = (ctypes.c_int64 * int(n_regions))()
+        with _Ordered(self):
+            _check(self._h, load_library().pct_solve_regions(self._h, int(n_regions), int(halo), int(iters),
+                                                              float(lam), int(block_size),
+                                                              ctypes.c_void_p(x.data_ptr()), cnt))
+        return list(cnt)
+
+    def fbp(self, n_angle, angle_step, n_t, t_min, dt, n_v, v_min, dv, out=None, sinogram=False):
+        """FBP initial iterate (CUDA float32, n voxels; 0 outside the hull), and
+        the filtered sinogram (n_angle, n_v, n_t) when ``sinogram``."""
+        import torch
+        x = torch.empty(self.n_vox, dtype=torch.float32, device=self.device) if out is None else out
+        q = torch.empty(int(n_angle) * int(n_v) * int(n_t), dtype=torch.float32,
+                        device=self.device) if sinogram else None
+        with _Ordered(self):
+            pct_fbp(self._h, self.n_vox, n_angle, angle_step, n_t, t_min, dt, n_v, v_min, dv, x, q)
+        return (x, q.view(int(n_angle), int(n_v), int(n_t))) if sinogram else x
 
     def build_rows(self):
         with _Ordered(self):

@@ -11,8 +11,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libpct.so")
 SOURCES = ["pct_api.cu", "pct_kernels.cu", "pct_rows.cu", "pct_grad.cu", "pct_batch.cu", "pct_noalloc.cu", "pct_peaks.cu",
-           "pct_clean.cu"]
-HEADERS = ["pct_device.cuh", "pct_warp.cuh", "pct_internal.h", "pct_batch.h"]
+           "pct_clean.cu", "pct_fbp.cu", "pct_regions.cu"]
+HEADERS = ["pct_device.cuh", "pct_warp.cuh", "pct_internal.h", "pct_batch.h", "pct_bins.cuh"]
 
 # --fmad=false: no implicit contraction of a*b+c, so every kernel that walks a
 # path (fused solve, stored-row builds, row dump, batch) computes bit-identical

@@ -59,6 +59,7 @@ struct pct_ctx {
     uint8_t* d_dist = nullptr;   // chessboard distance to the hull (hull search skipping)
     float4* d_sig1 = nullptr;
     int kmax = 0;
+    int kmax_floor = 0;                  // MLP table covers at least this many samples (region sub-contexts)
     int64_t du_um = 0;
     unsigned* d_flags = nullptr;
     unsigned long long* d_next = nullptr;   // work counter of the warp-per-proton kernels
@@ -185,7 +186,7 @@ pct_status build_sigma_table(pct_ctx* c)
     const double diag = std::sqrt(std::pow((double)c->grid.nx * c->grid.dx, 2) +
                                   std::pow((double)c->grid.ny * c->grid.dy, 2) +
                                   std::pow((double)c->grid.nz * c->grid.dz, 2));
-    const int kmax = (int)std::ceil(diag / du) + 3;
+    const int kmax = std::max((int)std::ceil(diag / du) + 3, c->kmax_floor);
     if (kmax > (1 << 22)) return fail(c, PCT_ERR_ARG, "MLP step too small for this grid");
     std::vector<float4> tab((size_t)kmax + 1);
     mlp_sigma_table(du, kmax, tab.data());
@@ -833,7 +834,7 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
                 e1 = next_event(c);
                 if (e0) cudaEventRecord(e0, c->stream);
             }
-            const float* b = c->d_hist + (size_t)H_WEPL * c->stride;
+            const float* b = c->d_hist ? c->d_hist + (size_t)H_WEPL * c->stride : nullptr;
             if (c->mode == PCT_MODE_CSR)
                 e = launch_drop_csr(L, c->d_flags, c->d_rowptr, c->d_idx, c->d_len, b, first, count, x, c->d_acc);
             else if (c->mode == PCT_MODE_PACKED)
@@ -872,7 +873,7 @@ pct_status pct_clean(pct_ctx* c, const pct_clean_params* p, uint8_t* keep_out, i
         if (n_kept) *n_kept = 0;
         return PCT_OK;
     }
-    const CleanBins P{p->n_angle, p->n_t, p->n_v, p->angle_step, p->t_min, p->dt, p->v_min, p->dv,
+    const CleanBins P{{p->n_angle, p->n_t, p->n_v, p->angle_step, p->t_min, p->dt, p->v_min, p->dv},
                       p->k_sigma};
     void *p_bin = nullptr, *p_cnt = nullptr, *p_sum = nullptr, *p_dev = nullptr, *p_keep = nullptr;
     void *p_chunk = nullptr, *p_total = nullptr, *p_new = nullptr;
@@ -915,6 +916,188 @@ pct_status pct_clean(pct_ctx* c, const pct_clean_params* p, uint8_t* keep_out, i
     c->rec_valid = false;
     if (n_kept) *n_kept = kept;
     return PCT_OK;
+}
+
+pct_status pct_solve_regions(pct_ctx* c, int32_t n_regions, int32_t halo, int32_t iters, float lambda,
+                             int64_t block_size, float* x, int64_t* region_protons)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!x) return fail(c, PCT_ERR_ARG, "null x");
+    const int nz = c->grid.nz;
+    if (n_regions < 1 || n_regions > nz) return fail(c, PCT_ERR_ARG, "regions must be 1..nz");
+    if (halo < 0) return fail(c, PCT_ERR_ARG, "negative overlap");
+    if (iters < 0 || block_size < 1 || !std::isfinite(lambda))
+        return fail(c, PCT_ERR_ARG, "iters < 0, block size < 1 or non-finite lambda");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s != PCT_OK) return s;
+    if ((s = prepare(c)) != PCT_OK) return s;
+    const int64_t plane = (int64_t)c->grid.nx * c->grid.ny;
+    const Launch L = launch_of(c);
+    // 1: setupImageRegions -- core slices [lo, hi), extended by `halo` slices
+    struct Region {
+        int lo, hi, elo, ehi;
+        int64_t count = 0;
+        pct_ctx* sub = nullptr;
+        float* x = nullptr;
+    };
+    std::vector<Region> R((size_t)n_regions);
+    for (int r = 0; r < n_regions; ++r) {
+        Region& g = R[(size_t)r];
+        g.lo = (int)((int64_t)r * nz / n_regions);
+        g.hi = (int)((int64_t)(r + 1) * nz / n_regions);
+        g.elo = std::max(0, g.lo - halo);
+        g.ehi = std::min(nz, g.hi + halo);
+    }
+    std::vector<uint8_t> mask((size_t)c->n_vox);
+    cudaError_t e = cudaMemcpyAsync(mask.data(), c->d_mask, (size_t)c->n_vox, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "hull mask read");
+    void *p_flag = nullptr, *p_chunk = nullptr, *p_total = nullptr;
+    auto cleanup = [&]() {
+        for (Region& g : R)
+            if (g.sub) pct_destroy(g.sub);
+        dfree(c, p_flag);
+        dfree(c, p_chunk);
+        dfree(c, p_total);
+    };
+    const int64_t n = c->n;
+    if ((s = dalloc(c, &p_flag, (size_t)std::max<int64_t>(n, 1), "region flags")) != PCT_OK ||
+        (s = dalloc(c, &p_chunk, (size_t)std::max<int64_t>(clean_chunks(n), 1) * sizeof(int64_t), "region scan")) != PCT_OK ||
+        (s = dalloc(c, &p_total, sizeof(int64_t), "region count")) != PCT_OK) {
+        cleanup();
+        return s;
+    }
+    for (Region& g : R) {
+        // a sub-context on the region's slab: same voxels, the hull slab, the
+        // same MLP spacing and a table as long as the full volume's
+        pct_grid sg = c->grid;
+        sg.nz = g.ehi - g.elo;
+        sg.oz = (float)((double)c->grid.oz + (double)g.elo * (double)c->grid.dz);
+        if ((s = pct_create(&g.sub, &sg, mask.data() + (size_t)g.elo * plane, c->device, c->stream)) != PCT_OK) {
+            s = fail(c, s, std::string("region context: ") + pct_last_error(nullptr));
+            cleanup();
+            return s;
+        }
+        pct_ctx* sub = g.sub;
+        sub->cta = c->cta;
+        sub->du_um = c->du_um;
+        sub->kmax_floor = c->kmax;
+        if ((s = build_sigma_table(sub)) != PCT_OK) {
+            s = fail(c, s, "region MLP table: " + sub->err);
+            cleanup();
+            return s;
+        }
+        // 2: identifyProtonsPassingRegions; 3: allocateMemoryForProtonsPerGPU
+        e = launch_region_flags(L, c->d_rec, c->stride, n, c->gc, g.elo, g.ehi, (uint8_t*)p_flag);
+        if (e == cudaSuccess) e = launch_flag_count(L, (uint8_t*)p_flag, n, (int64_t*)p_chunk, (int64_t*)p_total);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&g.count, p_total, sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(c, e, "region membership");
+        }
+        const int64_t stride = std::max<int64_t>((g.count + 31) / 32 * 32, 32);
+        void* p = nullptr;
+        if ((s = dalloc(sub, &p, (size_t)stride * R_NF * sizeof(float), "region records")) != PCT_OK) {
+            s = fail(c, s, "region records: " + sub->err);
+            cleanup();
+            return s;
+        }
+        sub->d_rec = (float*)p;
+        // records as the full volume computed them; the entry point's z moves
+        // into the slab's grid units
+        e = launch_flag_fill(L, (uint8_t*)p_flag, n, (int64_t*)p_chunk, c->d_rec, c->stride, R_NF, R_PZ,
+                             (float)-g.elo, sub->d_rec, stride);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(c, e, "region records");
+        }
+        sub->n = g.count;
+        sub->stride = stride;
+        sub->cap = stride;
+        sub->loaded = true;
+        sub->rec_valid = true;
+        if ((s = dalloc(sub, &p, (size_t)sg.nz * plane * sizeof(float), "region iterate")) != PCT_OK) {
+            s = fail(c, s, "region iterate: " + sub->err);
+            cleanup();
+            return s;
+        }
+        g.x = (float*)p;
+        e = cudaMemcpyAsync(g.x, x + (size_t)g.elo * plane, (size_t)sg.nz * plane * sizeof(float),
+                            cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(c, e, "region iterate copy");
+        }
+    }
+    // 4: iterativelySolvePerGPU -- the regions one after the other on this GPU
+    for (Region& g : R) {
+        if (g.count == 0) continue;
+        if ((s = pct_solve(g.sub, iters, lambda, block_size, g.x)) != PCT_OK) {
+            s = fail(c, s, "region solve: " + g.sub->err);
+            cleanup();
+            return s;
+        }
+        c->launches += g.sub->launches;
+        c->fused_launches += g.sub->fused_launches;
+    }
+    // 5: selectSlice -- each region's core slices make up the volume
+    for (Region& g : R) {
+        e = cudaMemcpyAsync(x + (size_t)g.lo * plane, g.x + (size_t)(g.lo - g.elo) * plane,
+                            (size_t)(g.hi - g.lo) * plane * sizeof(float), cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cleanup();
+            return cuda_fail(c, e, "region slice copy");
+        }
+    }
+    e = cudaStreamSynchronize(c->stream);
+    unsigned flags = 0;
+    for (Region& g : R) {
+        unsigned f = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&f, g.sub->d_flags, sizeof f, cudaMemcpyDeviceToHost);
+        flags |= f;
+    }
+    if (region_protons)
+        for (int r = 0; r < n_regions; ++r) region_protons[r] = R[(size_t)r].count;
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(c, e, "region solve");
+    if (flags) return fail(c, PCT_ERR_DEVICE, "device check failed in a region solve (flags " + std::to_string(flags) + ")");
+    return PCT_OK;
+}
+
+pct_status pct_fbp(pct_ctx* c, const pct_fbp_params* p, float* x, float* sino_out)
+{
+    if (!c) return PCT_ERR_ARG;
+    if (!p || !x) return fail(c, PCT_ERR_ARG, "null FBP parameters or x");
+    const int64_t nb = (int64_t)p->n_angle * p->n_t * p->n_v;
+    if (p->n_angle < 1 || p->n_angle > fbp_max_angles() || p->n_t < 1 || p->n_t > 16384 || p->n_v < 1 ||
+        nb > 0x7fffffffLL)
+        return fail(c, PCT_ERR_ARG, "FBP bins: 1..4096 angles, 1..16384 t bins, >= 1 v bin, < 2^31 bins");
+    if (!(p->angle_step > 0.0) || !(p->dt > 0.0) || !(p->dv > 0.0) || !std::isfinite(p->angle_step) ||
+        !std::isfinite(p->dt) || !std::isfinite(p->dv) || !std::isfinite(p->t_min) || !std::isfinite(p->v_min))
+        return fail(c, PCT_ERR_ARG, "FBP bin widths must be finite and > 0");
+    DeviceGuard dg(c->device);
+    pct_status s = need_histories(c);
+    if (s != PCT_OK) return s;
+    const ProtonBins P{p->n_angle, p->n_t, p->n_v, p->angle_step, p->t_min, p->dt, p->v_min, p->dv};
+    void *p_cnt = nullptr, *p_sum = nullptr, *p_q = nullptr;
+    if ((s = dalloc(c, &p_cnt, (size_t)nb * sizeof(unsigned), "FBP counts")) != PCT_OK ||
+        (s = dalloc(c, &p_sum, (size_t)nb * sizeof(double), "FBP sums")) != PCT_OK ||
+        (!sino_out && (s = dalloc(c, &p_q, (size_t)nb * sizeof(float), "FBP sinogram")) != PCT_OK)) {
+        dfree(c, p_cnt);
+        dfree(c, p_sum);
+        return s;
+    }
+    float* q = sino_out ? sino_out : (float*)p_q;
+    cudaError_t e = launch_fbp(launch_of(c), P, c->gc, c->d_mask, c->d_hist, c->stride, c->n, (unsigned*)p_cnt,
+                               (double*)p_sum, q, x);
+    // the scratch is freed once the kernels are done with it
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    dfree(c, p_cnt);
+    dfree(c, p_sum);
+    dfree(c, p_q);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "FBP");
 }
 
 pct_status pct_tv(pct_ctx* c, const float* x, float eps, float* grad, double* value)

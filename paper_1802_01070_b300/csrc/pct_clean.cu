@@ -18,6 +18,7 @@
 // rounding of a cut may be decided either way).  The library is compiled
 // without implicit multiply-add contraction, so the products and sums below
 // round as written.
+#include "pct_bins.cuh"
 #include "pct_internal.h"
 
 namespace pct {
@@ -25,25 +26,6 @@ namespace pct {
 namespace {
 
 constexpr int kCleanCta = 256;
-
-__device__ __forceinline__ int clean_bin(const CleanBins& P, double x0, double y0, double z0, double x1,
-                                         double y1, double z1, double phi)
-{
-    double s, c;
-    sincos(phi, &s, &c);
-    const double u0 = x0 * c + y0 * s, t0 = -x0 * s + y0 * c;
-    const double u1 = x1 * c + y1 * s, t1 = -x1 * s + y1 * c;
-    const double w = -u0 / (u1 - u0);
-    const double t = t0 + w * (t1 - t0);
-    const double v = z0 + w * (z1 - z0);
-    const double ka = floor(phi / P.angle_step + 0.5);
-    const double kt = floor((t - P.t_min) / P.dt);
-    const double kv = floor((v - P.v_min) / P.dv);
-    if (!(kt >= 0.0 && kt < (double)P.n_t && kv >= 0.0 && kv < (double)P.n_v) || !isfinite(ka)) return -1;
-    long long a = (long long)ka % P.n_angle;
-    if (a < 0) a += P.n_angle;
-    return (int)((a * P.n_v + (long long)kv) * P.n_t + (long long)kt);
-}
 
 __device__ __forceinline__ void clean_q(const float* __restrict__ h, int64_t stride, int64_t i, double q[3])
 {
@@ -59,7 +41,7 @@ k_clean_sum(CleanBins P, const float* __restrict__ h, int64_t stride, int64_t n,
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int b = clean_bin(P, h[H_INX * stride + i], h[H_INY * stride + i], h[H_INZ * stride + i],
+    const int b = proton_bin(P.bins, h[H_INX * stride + i], h[H_INY * stride + i], h[H_INZ * stride + i],
                             h[H_OUTX * stride + i], h[H_OUTY * stride + i], h[H_OUTZ * stride + i],
                             h[H_PHI * stride + i]);
     bin[i] = b;
@@ -166,9 +148,12 @@ k_keep_scan(int64_t* __restrict__ chunk, int64_t nchunks, int64_t* __restrict__ 
     if (threadIdx.x == kScanCta - 1) *total = part[threadIdx.x];
 }
 
+// ncols columns of `stride` floats are copied; column shift_col (if >= 0) gets
+// `shift` added on the way
 __global__ void __launch_bounds__(kCleanCta)
 k_keep_fill(const uint8_t* __restrict__ keep, int64_t n, const int64_t* __restrict__ chunk,
-            const float* __restrict__ h, int64_t stride, float* __restrict__ out, int64_t out_stride)
+            const float* __restrict__ h, int64_t stride, int ncols, int shift_col, float shift,
+            float* __restrict__ out, int64_t out_stride)
 {
     __shared__ int part[kCleanCta / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -187,8 +172,10 @@ k_keep_fill(const uint8_t* __restrict__ keep, int64_t n, const int64_t* __restri
         }
         if (v) {
             const int64_t pos = run + before + __popc(bal & ((1u << lane) - 1u));
-#pragma unroll
-            for (int f = 0; f < H_NF; ++f) out[f * out_stride + pos] = h[f * stride + i];
+            for (int f = 0; f < ncols; ++f) {
+                const float v = h[f * stride + i];
+                out[f * out_stride + pos] = f == shift_col ? v + shift : v;
+            }
         }
         run += total;
         __syncthreads();
@@ -206,7 +193,7 @@ cudaError_t launch_clean(const Launch& L, const CleanBins& P, const float* hist,
                          int* bin, unsigned* cnt, double* sum, double* dev2, uint8_t* keep)
 {
     if (n <= 0) return cudaSuccess;
-    const int64_t nb = (int64_t)P.n_angle * P.n_t * P.n_v;
+    const int64_t nb = (int64_t)P.bins.n_angle * P.bins.n_t * P.bins.n_v;
     cudaError_t e = cudaMemsetAsync(cnt, 0, (size_t)nb * sizeof(unsigned), L.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(sum, 0, (size_t)nb * 3 * sizeof(double), L.stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(dev2, 0, (size_t)nb * 3 * sizeof(double), L.stream);
@@ -219,17 +206,41 @@ cudaError_t launch_clean(const Launch& L, const CleanBins& P, const float* hist,
     return cudaGetLastError();
 }
 
+cudaError_t launch_flag_count(const Launch& L, const uint8_t* flag, int64_t n, int64_t* chunk, int64_t* total)
+{
+    if (n <= 0) return cudaMemsetAsync(total, 0, sizeof(int64_t), L.stream);
+    const int64_t nc = clean_chunks(n);
+    k_keep_count<<<(unsigned)nc, kCleanCta, 0, L.stream>>>(flag, n, chunk);
+    k_keep_scan<<<1, kScanCta, 0, L.stream>>>(chunk, nc, total);
+    *L.launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_fill(const Launch& L, const uint8_t* flag, int64_t n, const int64_t* chunk,
+                             const float* src, int64_t stride, int ncols, int shift_col, float shift, float* out,
+                             int64_t out_stride)
+{
+    if (n <= 0) return cudaSuccess;
+    k_keep_fill<<<(unsigned)clean_chunks(n), kCleanCta, 0, L.stream>>>(flag, n, chunk, src, stride, ncols,
+                                                                      shift_col, shift, out, out_stride);
+    ++*L.launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flag_compact(const Launch& L, const uint8_t* flag, int64_t n, int64_t* chunk,
+                                int64_t* total, const float* src, int64_t stride, int ncols, int shift_col,
+                                float shift, float* out, int64_t out_stride)
+{
+    cudaError_t e = launch_flag_count(L, flag, n, chunk, total);
+    if (e == cudaSuccess) e = launch_flag_fill(L, flag, n, chunk, src, stride, ncols, shift_col, shift, out, out_stride);
+    return e;
+}
+
 cudaError_t launch_keep_compact(const Launch& L, const uint8_t* keep, int64_t n, int64_t* chunk,
                                 int64_t* total, const float* hist, int64_t stride, float* out,
                                 int64_t out_stride)
 {
-    if (n <= 0) return cudaSuccess;
-    const int64_t nc = clean_chunks(n);
-    k_keep_count<<<(unsigned)nc, kCleanCta, 0, L.stream>>>(keep, n, chunk);
-    k_keep_scan<<<1, kScanCta, 0, L.stream>>>(chunk, nc, total);
-    k_keep_fill<<<(unsigned)nc, kCleanCta, 0, L.stream>>>(keep, n, chunk, hist, stride, out, out_stride);
-    *L.launches += 3;
-    return cudaGetLastError();
+    return launch_flag_compact(L, keep, n, chunk, total, hist, stride, H_NF, -1, 0.f, out, out_stride);
 }
 
 }  // namespace pct

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "pct_bins.cuh"
 #include "pct_device.cuh"
 
 namespace pct {
@@ -80,8 +81,8 @@ cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* 
 
 // data cleaning (pct_clean.cu): bins of (gantry angle, t, v) and the cut
 struct CleanBins {
-    int n_angle, n_t, n_v;
-    double angle_step, t_min, dt, v_min, dv, k_sigma;
+    ProtonBins bins;
+    double k_sigma;
 };
 // keep[i] = 1 for the protons within k_sigma of their bin's mean in WEPL and
 // both angle changes; bin (n), cnt (nbins), sum and dev2 (3 nbins) are scratch
@@ -93,6 +94,27 @@ int64_t clean_chunks(int64_t n);
 cudaError_t launch_keep_compact(const Launch& L, const uint8_t* keep, int64_t n, int64_t* chunk,
                                 int64_t* total, const float* hist, int64_t stride, float* out,
                                 int64_t out_stride);
+// the same compaction of any ncols float columns; column shift_col (>= 0) gets
+// `shift` added.  In two parts: count (chunk offsets and *total), then fill.
+cudaError_t launch_flag_count(const Launch& L, const uint8_t* flag, int64_t n, int64_t* chunk, int64_t* total);
+cudaError_t launch_flag_fill(const Launch& L, const uint8_t* flag, int64_t n, const int64_t* chunk,
+                             const float* src, int64_t stride, int ncols, int shift_col, float shift, float* out,
+                             int64_t out_stride);
+cudaError_t launch_flag_compact(const Launch& L, const uint8_t* flag, int64_t n, int64_t* chunk,
+                                int64_t* total, const float* src, int64_t stride, int ncols, int shift_col,
+                                float shift, float* out, int64_t out_stride);
+
+// image regions of Algorithm 1 (pct_regions.cu): flag[i] = proton i has a
+// hull path whose entry or exit slice lies in [lo, hi)
+cudaError_t launch_region_flags(const Launch& L, const float* rec, int64_t stride, int64_t n, const GridC& g,
+                                int lo, int hi, uint8_t* flag);
+
+// filtered back-projection (pct_fbp.cu): x = the FBP image inside the hull, 0
+// outside; cnt, sum (nbins) scratch, q (nbins) the filtered sinogram
+int fbp_max_angles();
+cudaError_t launch_fbp(const Launch& L, const ProtonBins& P, const GridC& g, const uint8_t* hull,
+                       const float* hist, int64_t stride, int64_t n, unsigned* cnt, double* sum, float* q,
+                       float* x);
 
 // gradient-based reconstruction (pct_grad.cu)
 cudaError_t launch_tv(const Launch& L, const float* x, int nx, int ny, int nz, float eps, float* grad,

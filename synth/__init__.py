@@ -355,3 +355,13 @@ def to_numpy(hist):
 
 def subset(hist, start, stop):
     return {k: v[start:stop] for k, v in hist.items()}
+
+
+def fbp_bins(cfg: ScanConfig) -> dict:
+    """Sinogram bins of the FBP initial iterate for a scan: one per gantry angle,
+    t bins of one voxel over the detector width, v bins of one voxel aligned
+    with the grid's slices."""
+    nx, _, nz = cfg.shape
+    return {"n_angle": cfg.n_angles, "angle_step": 2 * math.pi / cfg.n_angles, "n_t": nx,
+            "t_min": -0.5 * nx * cfg.voxel, "dt": cfg.voxel, "n_v": nz, "v_min": cfg.origin[2],
+            "dv": cfg.voxel}
