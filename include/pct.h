@@ -104,7 +104,21 @@ enum pct_option {
     /* pct_solve_batch with this context first: lanes per proton, 32 (one
      * proton per warp) or 16 (two per warp), when PCT_OPT_AUTOTUNE is off (the
      * autotuner picks it with the CTA size).  Default 32. */
-    PCT_OPT_BATCH_LANES = 11
+    PCT_OPT_BATCH_LANES = 11,
+    /* How the fused DROP block step (and pct_rows, which reports the rows that
+     * step uses) walks a proton's polyline (one of enum pct_walk).  Both give
+     * the same rows; performance only.  Default PCT_WALK_ROUNDS. */
+    PCT_OPT_WALK = 12
+};
+
+/* Walks of one proton's polyline by one warp (PCT_OPT_WALK). */
+enum pct_walk {
+    PCT_WALK_LANES = 0,  /* each lane walks a range of consecutive segments; runs that cross
+                            a lane boundary are joined by shuffles */
+    PCT_WALK_ROUNDS = 1  /* rounds of 32 segments, one per lane, walked with a fixed number of
+                            predicated steps; runs collected in shared memory, then gathered and
+                            scattered lane-strided (protons with more than 4 crossings in one
+                            segment, or more than 768 runs, take the lane walk) */
 };
 
 /* Row forms of pct_solve.  The stored forms are built by the same walk as the
@@ -143,7 +157,9 @@ enum pct_stat {
     PCT_STAT_BATCH_CTAS = 10,     /* CTAs of the last batched solve */
     PCT_STAT_GRAPH_REPLAYS = 11,  /* batched solves replayed from a CUDA graph */
     PCT_STAT_TIMED_LAUNCHES = 12, /* launches of the DROP block kernel timed (PCT_OPT_TIMING) */
-    PCT_STAT_BATCH_LANES = 13     /* lanes per proton of the last batched solve */
+    PCT_STAT_BATCH_LANES = 13,    /* lanes per proton of the last batched solve */
+    PCT_STAT_WALK_FALLBACKS = 14  /* DROP row walks PCT_WALK_ROUNDS passed to the lane walk
+                                     (synchronizes the stream) */
 };
 
 /* Create a context on CUDA device `device`: the reconstruction volume of

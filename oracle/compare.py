@@ -15,12 +15,14 @@ A voxel whose DROP inputs differ cannot be expected to match.
 
 The rule (one rule, for every test and the benchmark) has two parts.
 
-Row correctness.  A row that the oracle does not flag (margin >= NEAR_FACE_MM)
-must have the oracle's voxel sequence and every chord within chord_tol(cond) =
-CHORD_TOL_MM + POS_ERR_MM * cond, cond being the row's crossing conditioning
-(a crossing nearly parallel to its face moves along the path by the FP32
-sideways error over the sine of the angle).  A row that fails is counted as
-``unexcused``: a real disagreement, which the tests assert away.
+Row correctness.  cond is a row's crossing conditioning (path length per unit
+of travel across a crossed face): the FP32 path's position error POS_ERR_MM
+moves a crossing nearly parallel to its face by about POS_ERR_MM x cond, along
+the path and along the face.  The oracle flags a row when a crossing lies
+within NEAR_FACE_MM + POS_ERR_MM x cond of another face (near_face).  A row it
+does not flag must have the oracle's voxel sequence and every chord within
+chord_tol(cond) = CHORD_TOL_MM + POS_ERR_MM x cond; a row that fails is
+counted as ``unexcused``: a real disagreement, which the tests assert away.
 
 Voxel exclusion.  A hull voxel j is left out of an RSP comparison when its DROP
 inputs differ between the two sides:
@@ -40,7 +42,8 @@ import numpy as np
 NEAR_FACE_MM = 1e-4     # crossings this close to a voxel face may legitimately differ
 MLP_TOL_MM = 1e-3       # MLP point tolerance
 CHORD_TOL_MM = 2e-3     # chord tolerance (difference of two MLP-derived crossings)
-POS_ERR_MM = 1e-5       # sideways position error of the FP32 path (MLP points agree to ~6e-6 mm)
+POS_ERR_MM = 4e-5       # position error of the FP32 path: MLP points agree with the oracle's to
+                        # 6.5e-6 mm on the small scans and 3.3e-5 mm on the full-size ones
 
 
 def chord_tol(cond):
@@ -48,6 +51,13 @@ def chord_tol(cond):
     crossing conditioning (a crossing nearly parallel to its face moves along
     the path by the sideways error over the sine of the angle)."""
     return CHORD_TOL_MM + POS_ERR_MM * np.asarray(cond, dtype=np.float64)
+
+
+def near_face(margin, cond):
+    """Rows the oracle flags: a crossing within NEAR_FACE_MM of another voxel
+    face, widened by the distance POS_ERR_MM x cond by which the FP32 path's
+    position error can move a grazing crossing along the face."""
+    return np.asarray(margin) < NEAR_FACE_MM + POS_ERR_MM * np.asarray(cond, dtype=np.float64)
 
 
 def compare_row_chunk(gidx, glen, gnnz, rowptr, j, ln, margin, cond):
@@ -76,7 +86,7 @@ def compare_row_chunk(gidx, glen, gnnz, rowptr, j, ln, margin, cond):
     ll = np.where(valid, ln[pos] if ln.size else 0.0, 0.0)
     eq = same_n & np.all(~keep | (gidx == jj), axis=1)
     d = np.where(valid & eq[:, None], np.abs(glen - ll), 0.0)
-    flagged = np.asarray(margin) < NEAR_FACE_MM
+    flagged = near_face(margin, cond)
     wrong = (d > chord_tol(cond)[:, None]).any(axis=1) | ~eq
     unexcused = wrong & ~flagged
     vox = [gidx[d > CHORD_TOL_MM]]

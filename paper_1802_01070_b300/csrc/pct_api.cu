@@ -63,6 +63,7 @@ struct pct_ctx {
     int64_t du_um = 0;
     unsigned* d_flags = nullptr;
     unsigned long long* d_next = nullptr;   // work counter of the warp-per-proton kernels
+    unsigned long long* d_fallbacks = nullptr;   // protons the round walk passed to the lane walk
     bool loaded = false;                 // pct_load_histories has succeeded once
     bool rec_valid = false;              // the records match the loaded histories and MLP step
     int64_t n = 0, stride = 0, cap = 0;  // protons, column stride, column capacity
@@ -98,6 +99,7 @@ struct pct_ctx {
     int64_t spin_limit = 1 << 27;
     int batch_cta = 0, batch_ctas = 0, batch_lanes = 32;
     int lanes_opt = 32;                  // lanes per proton of batched solves (PCT_OPT_BATCH_LANES)
+    int walk = kWalkRounds;              // walk of the DROP step and the row writer (PCT_OPT_WALK)
     int64_t graph_replays = 0;
     ScanDesc* d_scans = nullptr;
     unsigned* d_bar = nullptr;
@@ -222,6 +224,8 @@ Geo geo_of(const pct_ctx* c)
     G.mask = c->d_mask;
     G.dist = c->d_dist;
     G.flags = c->d_flags;
+    G.walk = c->walk;
+    G.fallbacks = c->d_fallbacks;
     return G;
 }
 
@@ -510,6 +514,11 @@ pct_status pct_create(pct_ctx** out, const pct_grid* grid, const uint8_t* hull_m
     }
     if (s == PCT_OK && (s = dalloc(c, &p, sizeof(unsigned long long), "work counter")) == PCT_OK)
         c->d_next = (unsigned long long*)p;
+    if (s == PCT_OK && (s = dalloc(c, &p, sizeof(unsigned long long), "walk fallback counter")) == PCT_OK) {
+        c->d_fallbacks = (unsigned long long*)p;
+        e = cudaMemset(p, 0, sizeof(unsigned long long));
+        if (e != cudaSuccess) s = cuda_fail(c, e, "walk fallback counter");
+    }
     if (s == PCT_OK) s = build_sigma_table(c);
     if (s != PCT_OK) {
         g_create_error = "pct_create: " + c->err;
@@ -578,6 +587,10 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
     case PCT_OPT_AUTOTUNE:
         c->autotune = value ? 1 : 0;
         return PCT_OK;
+    case PCT_OPT_WALK:
+        if (value != PCT_WALK_LANES && value != PCT_WALK_ROUNDS) return fail(c, PCT_ERR_ARG, "unknown walk");
+        c->walk = (int)value;
+        return PCT_OK;
     case PCT_OPT_BATCH_LANES:
         if (value != 32 && value != 16) return fail(c, PCT_ERR_ARG, "lanes per proton must be 32 or 16");
         c->lanes_opt = (int)value;
@@ -618,6 +631,7 @@ pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
     case PCT_OPT_GRAPH: *value = c->graph; return PCT_OK;
     case PCT_OPT_AUTOTUNE: *value = c->autotune; return PCT_OK;
     case PCT_OPT_BATCH_LANES: *value = c->lanes_opt; return PCT_OK;
+    case PCT_OPT_WALK: *value = c->walk; return PCT_OK;
     case PCT_OPT_SPIN_LIMIT: *value = c->spin_limit; return PCT_OK;
     case PCT_OPT_TEST_UNREACHABLE_BARRIER: *value = c->test_unreachable; return PCT_OK;
     default: return PCT_ERR_ARG;
@@ -1452,6 +1466,14 @@ pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
     case PCT_STAT_BATCH_CTAS: *value = (double)c->batch_ctas; return PCT_OK;
     case PCT_STAT_BATCH_LANES: *value = (double)c->batch_lanes; return PCT_OK;
     case PCT_STAT_GRAPH_REPLAYS: *value = (double)c->graph_replays; return PCT_OK;
+    case PCT_STAT_WALK_FALLBACKS: {
+        unsigned long long v = 0;
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(&v, c->d_fallbacks, sizeof v, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(c, e, "fallback counter");
+        *value = (double)v;
+        return PCT_OK;
+    }
     default: return fail(c, PCT_ERR_ARG, "unknown stat key");
     }
 }
@@ -1474,6 +1496,10 @@ pct_status pct_tan_angle(const double* t, double* out, int64_t n, void* cuda_str
 pct_status pct_reset_stats(pct_ctx* c)
 {
     if (!c) return PCT_ERR_ARG;
+    if (c->d_fallbacks) {
+        DeviceGuard dg(c->device);
+        cudaMemsetAsync(c->d_fallbacks, 0, sizeof(unsigned long long), c->stream);
+    }
     c->launches = 0;
     c->fused_launches = 0;
     c->ev_used = 0;

@@ -21,12 +21,19 @@ struct Launch {
     int64_t* launches;    // launch counter to bump
 };
 
+// How the DROP block step and the row writer walk a proton's path: lane ranges
+// (pct_warp.cuh) or rounds of one segment per lane (pct_round.cuh).
+constexpr int kWalkLanes = 0;
+constexpr int kWalkRounds = 1;
+
 struct Geo {
     GridC g;
     MlpC mc;
     const uint8_t* mask;  // device, nx*ny*nz bytes
     const uint8_t* dist;  // device, nx*ny*nz bytes: chessboard distance to the hull (or null)
     unsigned* flags;      // device error word
+    int walk = kWalkLanes;
+    unsigned long long* fallbacks = nullptr;   // device: protons the round walk passed to the lane walk
 };
 
 // 1/(beta^2 p^2) of a 200 MeV proton in water as a polynomial in depth (cm),

@@ -6,6 +6,7 @@
 // MLP samples, then the voxel walk.  None of them stores A.  Also here: the
 // valid-proton lists of the DROP blocks and the hull distance map.
 #include "pct_internal.h"
+#include "pct_round.cuh"
 #include "pct_warp.cuh"
 
 namespace pct {
@@ -375,6 +376,146 @@ k_drop_fused(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, uns
     });
 }
 
+// The same DROP block step with the round walk (pct_round.cuh): the row is
+// built into the warp's run list, then s = a_i.x and q = ||a_i||^2 are gathered
+// and the scatter is issued lane-strided over the list.  A proton that does
+// not fit the round walk takes the lane-range walk (same shared memory).
+static_assert(kRoundRuns * 8 == kRunSlots * kWarp * 8, "run list and run slots share a warp's shared memory");
+
+// The lane-range DROP step of one proton, for the protons the round walk does
+// not fit; not inlined, so that its registers do not weigh on the round walk.
+__device__ __noinline__ void drop_proton_lanes(const Path& P, const MlpC& mc, const GridC& g,
+                                               const uint8_t* __restrict__ mask, unsigned* flags, RunSlots slots,
+                                               const float* __restrict__ x, float b, float2* acc)
+{
+    LaneWalk w;
+    float s, q;
+    warp_walk<kRunSlots, true>(P, mc, g, mask, x, flags, slots, mc.cmin, w, s, q);
+    if (!(q > 0.f)) return;
+    const float r = (b - s) / q;
+    replay_runs<kRunSlots>(P, mc, g, mask, flags, slots, w,
+                           [&](int j, float l) { atomicAdd(acc + j, make_float2(l * r, 1.f)); });
+}
+
+__global__ void __launch_bounds__(kWarpCta, kWarpCtaMin)
+k_drop_rounds(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
+              const int64_t* __restrict__ vidx, const int64_t* __restrict__ boff, int64_t k,
+              const float* __restrict__ x, float2* acc, unsigned long long* next, int first,
+              unsigned long long* fallbacks)
+{
+    extern __shared__ unsigned char smem[];
+    const RunSlots slots = warp_slots(smem, kRunSlots);
+    const RunList list{slots.j, slots.l};
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int64_t lo = boff[k];
+    for_each_item(boff[k + 1] - lo, first, next, [&](int64_t t) {
+        const int64_t i = vidx[lo + t];
+        Path P;
+        if (!load_path(rv, i, mc, P)) return;
+        int total = 0;
+        if (round_runs(P, mc, g, list, total)) {
+            float s = 0.f, q = 0.f;
+            for (int e = lane; e < total; e += kWarp) {
+                int j = list.j[e];
+                const float l = list.l[e];
+                if (j >= 0) {
+                    if (__ldg(mask + j)) {
+                        s = fmaf(l, __ldg(x + j), s);
+                        q = fmaf(l, l, q);
+                    } else {
+                        j = -1;
+                    }
+                }
+                list.j[e] = j;   // the hull decision, for the scatter below
+            }
+#pragma unroll
+            for (int o = kWarp / 2; o > 0; o >>= 1) {
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+                q += __shfl_xor_sync(0xffffffffu, q, o);
+            }
+            if (q > 0.f) {
+                const float r = (rv.get(R_B, i) - s) / q;
+                for (int e = lane; e < total; e += kWarp) {
+                    const int j = list.j[e];
+                    if (j >= 0) atomicAdd(acc + j, make_float2(list.l[e] * r, 1.f));
+                }
+            }
+            __syncwarp();
+            return;
+        }
+        if (fallbacks && lane == 0) atomicAdd(fallbacks, 1ull);
+        drop_proton_lanes(P, mc, g, mask, flags, slots, x, rv.get(R_B, i), acc);
+        __syncwarp();
+    });
+}
+
+// Rows of A in path order with the round walk (debug / parity): what
+// k_drop_rounds scatters.  Two warps per CTA; a proton that does not fit the
+// round walk takes the lane-range walk of k_rows.
+__global__ void __launch_bounds__(64)
+k_rows_rounds(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsigned* flags,
+              int64_t first, int64_t count, int32_t max_nnz, int32_t* __restrict__ idx,
+              float* __restrict__ len, int32_t* __restrict__ nnz)
+{
+    extern __shared__ unsigned char smem[];
+    const int lane = threadIdx.x & (kWarp - 1);
+    const int64_t t = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (t >= count) return;
+    Path P;
+    if (!load_path(rv, first + t, mc, P)) {
+        if (lane == 0) nnz[t] = 0;
+        return;
+    }
+    const RunSlots slots = warp_slots(smem, kRowSlots);
+    const RunList list{slots.j, slots.l};
+    int32_t* oi = idx + t * (int64_t)max_nnz;
+    float* ol = len + t * (int64_t)max_nnz;
+    int total = 0;
+    if (round_runs(P, mc, g, list, total)) {
+        if (lane == 0) {
+            int n = 0;
+            for (int e = 0; e < total; ++e) {
+                const int j = list.j[e];
+                if (j < 0 || !__ldg(mask + j)) continue;
+                if (n < max_nnz) {
+                    oi[n] = j;
+                    ol[n] = list.l[e];
+                }
+                ++n;
+            }
+            nnz[t] = n;
+        }
+        return;
+    }
+    LaneWalk w;
+    float s, q;
+    warp_walk<kRowSlots, false>(P, mc, g, mask, nullptr, flags, slots, mc.cmin, w, s, q);
+    if (__any_sync(0xffffffffu, w.n > kRowSlots)) {
+        if (lane == 0) {
+            nnz[t] = -1;
+            atomicOr(flags, kFlagRowSlots);
+        }
+        return;
+    }
+    int mine = (w.k0 < w.k1) ? w.n - ((w.merged_prev && w.head_in) ? 1 : 0) : 0;
+    int off = mine;
+#pragma unroll
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += v;
+    }
+    const int tot = __shfl_sync(0xffffffffu, off, kWarp - 1);
+    off -= mine;
+    replay_runs<kRowSlots>(P, mc, g, mask, flags, slots, w, [&](int j, float l) {
+        if (off < max_nnz) {
+            oi[off] = j;
+            ol[off] = l;
+        }
+        ++off;
+    });
+    if (lane == 0) nnz[t] = tot;
+}
+
 // DROP block apply (Sec. IV-B): x_j += lambda * num_j / s_j where the block touched
 // voxel j, and clear the accumulator for the next block.
 // `next` (if not null): the work counter of the block step, reset here for
@@ -484,11 +625,11 @@ cudaError_t launch_rows(const Launch& L, const Geo& G, const float* rec, int64_t
     if (count <= 0) return cudaSuccess;
     const int cta = 64;   // 2 warps: the row writer keeps 64 slots per lane
     const size_t sm = slot_bytes(cta, kRowSlots);
-    cudaError_t e = allow_smem(k_rows, sm);
+    const auto kern = G.walk == kWalkRounds ? k_rows_rounds : k_rows;
+    cudaError_t e = allow_smem(kern, sm);
     if (e != cudaSuccess) return e;
-    k_rows<<<warp_grid(count, cta), cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask,
-                                                         G.flags, first, count, max_nnz, out_idx,
-                                                         out_len, out_nnz);
+    kern<<<warp_grid(count, cta), cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, first,
+                                                       count, max_nnz, out_idx, out_len, out_nnz);
     PCT_LAUNCH_TAIL(L);
 }
 
@@ -557,13 +698,22 @@ cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, i
 {
     if (count <= 0) return cudaSuccess;
     const size_t sm = slot_bytes(L.cta, kRunSlots);
-    cudaError_t e = allow_smem(k_drop_fused, sm);
     unsigned grid;
     int first;
-    if (e == cudaSuccess) e = item_shape(k_drop_fused, L.cta, sm, count, grid, first);
-    if (e != cudaSuccess) return e;
-    k_drop_fused<<<grid, L.cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff,
-                                                k, x, acc, next, first);
+    cudaError_t e;
+    if (G.walk == kWalkRounds) {
+        e = allow_smem(k_drop_rounds, sm);
+        if (e == cudaSuccess) e = item_shape(k_drop_rounds, L.cta, sm, count, grid, first);
+        if (e != cudaSuccess) return e;
+        k_drop_rounds<<<grid, L.cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff,
+                                                     k, x, acc, next, first, G.fallbacks);
+    } else {
+        e = allow_smem(k_drop_fused, sm);
+        if (e == cudaSuccess) e = item_shape(k_drop_fused, L.cta, sm, count, grid, first);
+        if (e != cudaSuccess) return e;
+        k_drop_fused<<<grid, L.cta, sm, L.stream>>>(G.g, G.mc, RecView{rec, stride}, G.mask, G.flags, vidx, boff,
+                                                    k, x, acc, next, first);
+    }
     PCT_LAUNCH_TAIL(L);
 }
 

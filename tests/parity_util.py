@@ -9,7 +9,7 @@ import torch
 import oracle as O
 import synth
 from oracle.compare import (CHORD_TOL_MM, MLP_TOL_MM, NEAR_FACE_MM, POS_ERR_MM, Exclusion,  # noqa: F401
-                            chord_tol, solve_parity)
+                            chord_tol, near_face, solve_parity)
 
 
 @functools.lru_cache(maxsize=8)
@@ -71,7 +71,7 @@ def compare_rows(gidx, glen, gnnz, rowptr, j, ln, margin, cond=None, dL=None,
             if d > tol:
                 bad.append((i, "chord", d))
             continue
-        if margin[i] < NEAR_FACE_MM:
+        if near_face(margin[i], cond[i] if cond is not None else 0.0):
             excused += 1
             if dL is not None:
                 dtot = abs(float(gl.sum()) - float(ol.sum()))

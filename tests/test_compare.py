@@ -7,7 +7,7 @@ the row's crossing conditioning, and that DROP counts are compared per block.
 """
 import numpy as np
 
-from oracle.compare import NEAR_FACE_MM, Exclusion, chord_tol, compare_row_chunk, solve_parity
+from oracle.compare import NEAR_FACE_MM, Exclusion, chord_tol, compare_row_chunk, near_face, solve_parity
 
 
 def _rows():
@@ -59,6 +59,8 @@ def test_chord_difference_excludes_its_voxel_and_fails_unflagged_rows():
     assert chord_tol(2000.0) > 0.01
     r = compare_row_chunk(gi, gl, nnz, rowptr, j, ln, margin, cond)
     assert r["unexcused"].size == 0 and r["chord_vox"].tolist() == [5]
+    # the near-face window widens with the conditioning
+    assert not near_face(2 * NEAR_FACE_MM, 1.0) and near_face(2 * NEAR_FACE_MM, 1000.0)
     # below the flat chord tolerance nothing is excluded
     gl[1, 1] = ln[4] + 0.001
     r = compare_row_chunk(gi, gl, nnz, rowptr, j, ln, np.ones(3), np.ones(3))
