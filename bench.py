@@ -502,9 +502,10 @@ def run_ours(args):
         out["rsp_err_vs_fp64"] = dict(
             par, sample="same %d-proton sample, GPU FP32 %s vs oracle FP64; 'clean' = hull voxels the "
                         "comparison rule keeps: DROP count s_j identical on both sides in every block, "
-                        "and no near-face row (oracle margin < 1e-4 mm) crossing the voxel with chords "
-                        "that differ by more than 2e-3 mm + 1e-5 mm x the row's crossing conditioning"
-                        % (s, args.mode))
+                        "and no row crossing the voxel with chords that differ by more than 2e-3 mm; "
+                        "rows_unexcused = rows that differ from the oracle's beyond 2e-3 mm + 4e-5 mm x "
+                        "their crossing conditioning without an oracle near-face flag; each side on its "
+                        "own trajectory (free-running)" % (s, args.mode))
     if rank == 0:
         print(json.dumps(out))
     ctx.close()
@@ -812,18 +813,22 @@ def run_fbp(args):
         torch.cuda.synchronize(dev)
         ts.append(e0.elapsed_time(e1))
     fbp_ms = statistics.median(ts)
-    curves = {}
-    for name, start in (("ones", hm.float()), ("fbp", x_fbp)):
-        x = start.clone()
-        r, err, ins = _quality(ctx, x, b, valid, hm, truth)
-        curve = [{"iter": 0, "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins}]
-        for it in range(cfg.iters):
-            ctx.solve(x, 1, cfg.lam, block)
+    curves, reach = {}, {}
+    for lam in (cfg.lam, 0.1):
+        for name, start in (("ones", hm.float()), ("fbp", x_fbp)):
+            x = start.clone()
             r, err, ins = _quality(ctx, x, b, valid, hm, truth)
-            curve.append({"iter": it + 1, "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins})
-        curves[name] = curve
-    target = curves["ones"][-1]["residual"]
-    reach = next((c["iter"] for c in curves["fbp"] if c["residual"] <= target), None)
+            curve = [{"iter": 0, "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins}]
+            for it in range(cfg.iters):
+                ctx.solve(x, 1, lam, block)
+                r, err, ins = _quality(ctx, x, b, valid, hm, truth)
+                curve.append({"iter": it + 1, "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins})
+            curves["%s, lambda %g" % (name, lam)] = curve
+        # iterations from the FBP start to within 0.1 % of the x0 = 1 start's
+        # final residual
+        target = curves["ones, lambda %g" % lam][-1]["residual"] * 1.001
+        reach["lambda %g" % lam] = next((c["iter"] for c in curves["fbp, lambda %g" % lam]
+                                         if c["residual"] <= target), None)
     print(json.dumps({
         "metric": "FBP initial iterate: ms per FBP and DROP iterations to the x0=1 start's final residual",
         "value": fbp_ms, "unit": "ms", "higher_is_better": False,
@@ -877,7 +882,9 @@ def run_regions(args):
     valid = ctx.hull_states()[:, 10] > 0.5
     block = args.block or cfg.block
     res = {}
-    for name, regions, halo in (("plain", 0, 0), ("2 regions", 2, 3), ("4 regions", 4, 3)):
+    # overlap: the paper's three 2.5 mm slices on each side, 7.5 mm
+    halo = int(math.ceil(7.5 / cfg.voxel))
+    for name, regions in (("plain", 0), ("2 regions", 2), ("4 regions", 4)):
         times = []
         for k in range(2):
             x = hm.float()
@@ -893,8 +900,11 @@ def run_regions(args):
             torch.cuda.synchronize(dev)
             times.append(e0.elapsed_time(e1))
         r, err, ins = _quality(ctx, x, b, valid, hm, truth)
-        res[name] = {"ms": times[-1], "protons_per_region": counts, "halo_slices": halo, "residual": r,
-                     "rsp_mean_abs_rel_err": err, "inserts": ins}
+        res[name] = {"ms": times[-1], "protons_per_region": counts, "halo_slices": halo if regions else 0,
+                     "residual": r, "rsp_mean_abs_rel_err": err, "inserts": ins}
+        if regions:
+            # protons that fit no region (both hull end points in one region's slices)
+            res[name]["note"] = "a proton may belong to two regions, or to none"
     print(json.dumps({"metric": "image regions (Algorithm 1) on one GPU vs the plain solve",
                       "config": {"workload": "%s: %d protons, %d iterations, block %d" % (
                           cfg.name, ctx.n, cfg.iters, block)}, "results": res}))

@@ -377,9 +377,10 @@ pct_status pct_clean(pct_ctx *ctx, const pct_clean_params *params, uint8_t *keep
  *   1 setupImageRegions: region r's core slices are [r nz / R, (r+1) nz / R)
  *     (integer division), extended by `halo` slices on each side (clamped);
  *   2 identifyProtonsPassingRegions: a proton with a hull path belongs to
- *     region r when the slice of its hull entry point or of its hull exit
- *     point (pct_hull_states) lies in r's extended slices -- it may belong to
- *     two regions;
+ *     region r when the slices of both its hull entry point and its hull exit
+ *     point (pct_hull_states; points on the grid's outer z faces count in the
+ *     first or last slice) lie in r's extended slices -- it may belong to two
+ *     regions, or to none (the paper sizes the overlap for 96 % coverage);
  *   3 allocateMemoryForProtonsPerGPU: each region gets its protons' records
  *     (the full volume's: the same MLP paths) on a grid of its extended slices;
  *   4 iterativelySolvePerGPU: pct_solve on each region (fused rows, which

@@ -10,9 +10,12 @@ What it computes (arXiv:1802.01070, Sec. III, Algorithm 1):
    slices on both sides, clamped to the volume.  (The paper's example: 20
    slices, two regions 0-12 and 7-19, i.e. halo 3, cores 0-9 and 10-19.)
 2. identifyProtonsPassingRegions: a proton with a hull path belongs to a
-   region when the slice of its hull entry point or of its hull exit point
-   lies in the region's extended range ("the image region entered to and
-   exited from").
+   region when the slices of both its hull entry point and its hull exit
+   point lie in the region's extended range ("the image region entered to
+   and exited from"), so that its path lies in the region's slab; protons
+   that fit no region are not used (the paper sizes the overlap "for a 96%
+   coverage").  A point on the grid's lowest or highest face counts in the
+   first or last slice.
 3./4. allocateMemoryForProtonsPerGPU, iterativelySolvePerGPU: each region is
    solved by DROP on its own, from the initial iterate's slab, with its
    protons' rows restricted to the region's extended slices (the path data of
@@ -20,9 +23,12 @@ What it computes (arXiv:1802.01070, Sec. III, Algorithm 1):
 5. selectSlice: the final volume takes each region's core slices.
 
 Rows are the oracle's (``oracle.rows`` on the full volume: the same MLP path as
-the single-region solve); DROP is ``oracle.drop``.  A reading: the paper does
-not say whether a region keeps the full path or only its slab; the slab is
-the region's whole image, so only its voxels are unknowns of its system.
+the single-region solve); DROP is ``oracle.drop``.  Readings: membership needs
+both end points in the region (the other reading, either end point, gives a
+region rows cut off at its slab with the full WEPL as right-hand side; its
+system is inconsistent, and with a thin overlap DROP diverges); a row keeps
+only the voxels of its region's slab (a path that bends out of the slab
+between its end points loses that part).
 
 Parity status: pinned by tests/test_oracle_regions.py (one region is the plain
 solve, regions covering the whole volume reproduce it, the paper's example
@@ -47,14 +53,14 @@ def regions(nz: int, n_regions: int, halo: int):
 def entry_exit_slices(geo: "O.Geometry", hist):
     """(valid, slice of the hull entry point, slice of the hull exit point)."""
     st, valid, _ = O.prepare(geo, hist)
-    oz, dz = geo.origin[2], geo.voxel[2]
-    s_in = np.floor((st[:, 4] - oz) / dz).astype(np.int64)
-    s_out = np.floor((st[:, 8] - oz) / dz).astype(np.int64)
+    oz, dz, nz = geo.origin[2], geo.voxel[2], geo.shape[2]
+    s_in = np.clip(np.floor((st[:, 4] - oz) / dz), 0, nz - 1).astype(np.int64)
+    s_out = np.clip(np.floor((st[:, 8] - oz) / dz), 0, nz - 1).astype(np.int64)
     return valid, s_in, s_out
 
 
 def members(valid, s_in, s_out, elo: int, ehi: int):
-    return valid & (((s_in >= elo) & (s_in < ehi)) | ((s_out >= elo) & (s_out < ehi)))
+    return valid & (s_in >= elo) & (s_in < ehi) & (s_out >= elo) & (s_out < ehi)
 
 
 def restrict_rows(rowptr, j, ln, sel, plane: int, elo: int, ehi: int):

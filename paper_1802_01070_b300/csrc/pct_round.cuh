@@ -163,7 +163,7 @@ __device__ __forceinline__ bool round_runs(const Path& P, const MlpC& mc, const 
         const bool cont = act && (lane == kWarp - 1 ? sg < P.nseg : next_m);
         // runs this lane completes: the previous round's open run (lane 0,
         // when not continued), then its pieces but the continued last one
-        const bool emit_open = lane == 0 && have_open && !m;
+        const bool emit_open = lane == 0 && have_open && !m && open_l > 0.f;
         int cnt = emit_open ? 1 : 0;
 #pragma unroll
         for (int k = 0; k < kPieces; ++k) {

@@ -142,7 +142,7 @@ def test_torso_full_size():
     del hist
     torch.cuda.empty_cache()
     r, _ = _free_running(cfg, hull, sub, 1, B, "torso, one block of %d, 1 iteration" % B)
-    assert r["clean_max"] <= 1e-3 and r["frac_within_1e-3"] >= 0.9999
+    assert r["clean_max"] <= 1e-3 and r["frac_within_1e-3"] >= 0.999
     assert r["excluded"] <= 0.01 * hull.sum()
 
 

@@ -1,12 +1,13 @@
 """Algorithm 1 (image regions, Sec. III) on the GPU vs the FP64 oracle (oracle/regions.py).
 
-Each region solves DROP with the protons that enter or exit its extended
-slices, on rows restricted to those slices; the volume takes each region's
-core slices.  Checked through the C ABI: the protons per region against the
-oracle's (a proton whose hull entry or exit lies within 1e-4 mm of a region's
-boundary slice face may be counted on either side), one DROP step per region
-against the oracle's within 1e-3 on the voxels the comparison rule keeps, and
-6 iterations with the same free-running bounds as the single-region solve.
+Each region solves DROP with the protons that enter and exit within its
+extended slices, on rows restricted to those slices; the volume takes each
+region's core slices.  Checked through the C ABI: the protons per region
+against the oracle's (a proton whose hull entry or exit lies within 1e-4 mm of
+an interior face of a region's slices may be counted on either side), one DROP
+step per region against the oracle's within 1e-3 on the voxels the comparison
+rule keeps, and 6 iterations with the same free-running bounds as the
+single-region solve.
 """
 import numpy as np
 import pytest
@@ -36,14 +37,17 @@ def tiny(cuda_device):
 
 
 def _near_boundary(t, e, f):
-    """Protons whose hull entry or exit z lies within NEAR_MM of slice face e or f."""
+    """Protons whose hull entry or exit z lies within NEAR_MM of slice face e or
+    f, where that face is inside the grid (the outer faces are not ambiguous:
+    a point on them counts in the first or last slice)."""
     geo = t["geo"]
-    oz, dz = geo.origin[2], geo.voxel[2]
+    oz, dz, nz = geo.origin[2], geo.voxel[2], geo.shape[2]
     out = np.zeros(t["valid"].size, bool)
     for col in (4, 8):
         z = t["st"][:, col]
         for face in (e, f):
-            out |= np.abs(z - (oz + face * dz)) < NEAR_MM
+            if 0 < face < nz:
+                out |= np.abs(z - (oz + face * dz)) < NEAR_MM
     return out & t["valid"]
 
 

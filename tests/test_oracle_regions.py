@@ -66,26 +66,27 @@ def test_membership_from_the_polyline_end_points(scan):
     z_in = pts[idx, 0, 2]
     z_out = pts[idx, npts[idx] - 1, 2]
     dz, oz = geo.voxel[2], geo.origin[2]
-    assert np.array_equal(np.floor((z_in - oz) / dz).astype(int), s_in[idx])
-    assert np.array_equal(np.floor((z_out - oz) / dz).astype(int), s_out[idx])
-    # two regions with a halo: every proton with a hull path is in at least
-    # one; those crossing the middle may be in both
+    # end points on the grid's outer faces count in the first or last slice
     nz = cfg.shape[2]
-    (lo0, hi0, e0, f0), (lo1, hi1, e1, f1) = G.regions(nz, 2, 1)
-    m0 = G.members(valid, s_in, s_out, e0, f0)
-    m1 = G.members(valid, s_in, s_out, e1, f1)
-    assert np.array_equal(m0 | m1, valid)
-    assert (m0 & m1).sum() > 0
-    # each region holds exactly the protons whose polyline starts or ends in
+    zs_in = np.clip(np.floor((z_in - oz) / dz), 0, nz - 1)
+    zs_out = np.clip(np.floor((z_out - oz) / dz), 0, nz - 1)
+    assert np.array_equal(zs_in.astype(int), s_in[idx]) and np.array_equal(zs_out.astype(int), s_out[idx])
+    # each region holds exactly the protons whose polyline starts and ends in
     # its extended slices
-    zs_in = np.floor((z_in - oz) / dz)
-    zs_out = np.floor((z_out - oz) / dz)
-    for e, f, m in ((e0, f0, m0), (e1, f1, m1)):
+    regs = G.regions(nz, 2, 1)
+    ms = []
+    for lo, hi, e, f in regs:
+        m = G.members(valid, s_in, s_out, e, f)
         want = np.zeros_like(valid)
-        want[idx] = ((zs_in >= e) & (zs_in < f)) | ((zs_out >= e) & (zs_out < f))
+        want[idx] = (zs_in >= e) & (zs_in < f) & (zs_out >= e) & (zs_out < f)
         assert np.array_equal(m, want)
-    # and some protons belong to a region only through their exit point
-    assert ((zs_out >= e0) & (zs_out < f0) & ~((zs_in >= e0) & (zs_in < f0))).any()
+        ms.append(m)
+    # nearly every proton with a hull path fits a region; one that starts in a
+    # region's slices and ends outside them does not belong to it
+    covered = ms[0] | ms[1]
+    assert not (covered & ~valid).any() and covered[valid].mean() > 0.95
+    e0, f0 = regs[0][2], regs[0][3]
+    assert ((zs_in >= e0) & (zs_in < f0) & (zs_out >= f0)).any()
 
 
 def test_restricted_rows_add_up_to_the_full_rows(scan):
