@@ -54,6 +54,8 @@ def _args():
                         "reconstruction with the differentiable projector (workload 'diff')")
     p.add_argument("--mode", default="fused", choices=["fused", "csr", "packed"],
                    help="row form: recomputed on the fly, or stored (built once, timed apart)")
+    p.add_argument("--walk", default=None, choices=["rounds", "lanes"],
+                   help="walk of the fused DROP step (default: the library's, rounds)")
     p.add_argument("--chord", default="fixed16", choices=["fixed16", "fp16"],
                    help="chord code of the packed rows")
     p.add_argument("--cpu-sample", type=int, default=320000)
@@ -145,7 +147,7 @@ def fused_flops(n_valid, mean_pts, mean_nnz):
 
 
 # the sources the fused block kernel is compiled from (host code excluded)
-KERNEL_SOURCES = ("pct_device.cuh", "pct_kernels.cu", "pct_warp.cuh")
+KERNEL_SOURCES = ("pct_device.cuh", "pct_kernels.cu", "pct_warp.cuh", "pct_round.cuh")
 
 
 def _kernel_hash():
@@ -315,6 +317,9 @@ def run_ours(args):
     ctx.set_option(pct.PCT_OPT_MODE, mode)
     ctx.set_option(pct.PCT_OPT_CHORD_CODE,
                    pct.PCT_CHORD_FIXED16 if args.chord == "fixed16" else pct.PCT_CHORD_FP16)
+    if args.walk:
+        ctx.set_option(pct.PCT_OPT_WALK, {"rounds": pct.PCT_WALK_ROUNDS, "lanes": pct.PCT_WALK_LANES}[args.walk])
+    walk = ctx.get_option(pct.PCT_OPT_WALK)
     ctx.load_histories(hist)
     build_s = None
     if mode != pct.PCT_MODE_FUSED:
@@ -401,7 +406,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": (per_row_traffic * valid / blocks_per_iter) if per_row_traffic else None,
-                "kernel": "k_drop_fused", "avg_launch_ms": avg_launch_s * 1e3,
+                "kernel": "k_drop_rounds" if walk == pct.PCT_WALK_ROUNDS else "k_drop_fused",
+                "avg_launch_ms": avg_launch_s * 1e3,
                 "launches_timed": timed_n, "launches": fused_n,
                 "peak_source": "measured: pct_peak_fp32, FP32 FMA loop filling every SM (best of 5, "
                                "CUDA events), in this run",

@@ -72,7 +72,7 @@ def _L():
         P = ctypes.c_void_p
         lib.o_sigma.argtypes = [P, ctypes.c_double, ctypes.c_double, P]
         lib.o_mlp_point.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, P]
-        lib.o_hull_entry.argtypes = [P, P, P, P, ctypes.c_double, P, P]
+        lib.o_hull_entry.argtypes = [P, P, P, P, ctypes.c_double, P, P, P]
         lib.o_prepare.argtypes = [P, P, ctypes.c_int64, P, P, P, P]
         lib.o_mlp_points.argtypes = [P, P, ctypes.c_int64, P, ctypes.c_int32, P, P]
         lib.o_rows.argtypes = [P, P, ctypes.c_int64, P, P, P, P, P, P]
@@ -168,13 +168,18 @@ def mlp_point(geo: Geometry, y0, y2, L: float, u1: float) -> np.ndarray:
     return out
 
 
-def hull_entry(geo: Geometry, T, D, S: float):
-    """(hit, s_hit, margin) for the line T + s D, s in [0, S]."""
+def hull_entry(geo: Geometry, T, D, S: float, with_cond: bool = False):
+    """(hit, s_hit, margin) for the line T + s D, s in [0, S]; with ``with_cond``
+    also the conditioning of the crossing into the hit voxel (the line's length
+    per unit of travel across the crossed face; 1 if it starts inside)."""
     t = np.ascontiguousarray(T, dtype=np.float64)
     d = np.ascontiguousarray(D, dtype=np.float64)
     s = np.zeros(1)
     m = np.full(1, np.inf)
-    hit = _L().o_hull_entry(geo._cp(), geo._mp(), _ptr(t), _ptr(d), float(S), _ptr(s), _ptr(m))
+    c = np.ones(1)
+    hit = _L().o_hull_entry(geo._cp(), geo._mp(), _ptr(t), _ptr(d), float(S), _ptr(s), _ptr(m), _ptr(c))
+    if with_cond:
+        return bool(hit), float(s[0]), float(m[0]), float(c[0])
     return bool(hit), float(s[0]), float(m[0])
 
 
@@ -212,7 +217,9 @@ def rows(geo: Geometry, hist, with_cond: bool = False):
     boundary to a voxel face -- rows below 1e-4 mm are near-face cases.
     With ``with_cond`` a fifth array gives, per row, the largest ratio of
     segment length to its extent across a crossed face (how much a sideways
-    position error moves a crossing along the path; 1 for a head-on crossing).
+    position error moves a crossing along the path; 1 for a head-on crossing),
+    over the walk's crossings and the tracker lines' crossings into their first
+    hull voxels.
     """
     keep, arr, n = _hist_arrays(hist)
     rowptr = np.zeros(n + 1, dtype=np.int64)

@@ -179,14 +179,19 @@ static double o_face_dist(double pos, double o, double d)
 /* Straight line p(s) = T + s D, s in [0, S], D in lab mm per mm of depth.
  * On a hit returns 1 and *s_hit = parameter where the line first enters a
  * voxel whose mask byte is nonzero.  *margin (if not NULL) is lowered to the
- * smallest distance (mm) between a crossing point and a face of another axis. */
+ * smallest distance (mm) between a crossing point and a face of another axis.
+ * *cond (if not NULL) is raised to the conditioning of the crossing into the
+ * hit voxel: the line's length per unit of travel across the crossed face,
+ * |D| / |D_a| (1 when the line starts inside that voxel) -- how far a
+ * position error moves that crossing along the line. */
 int o_hull_entry(const o_cfg *g, const uint8_t *mask, const double T[3], const double D[3],
-                 double S, double *s_hit, double *margin)
+                 double S, double *s_hit, double *margin, double *cond)
 {
     const int32_t n[3] = {g->nx, g->ny, g->nz};
     const double d[3] = {g->dx, g->dy, g->dz};
     const double o[3] = {g->ox, g->oy, g->oz};
     double s_lo = 0.0, s_hi = S;
+    int cross_axis = -1; /* axis of the face crossed into the current voxel */
     for (int a = 0; a < 3; ++a) {
         double lo = o[a], hi = o[a] + n[a] * d[a];
         if (D[a] == 0.0) {
@@ -194,10 +199,11 @@ int o_hull_entry(const o_cfg *g, const uint8_t *mask, const double T[3], const d
         } else {
             double s1 = (lo - T[a]) / D[a], s2 = (hi - T[a]) / D[a];
             if (s1 > s2) { double tmp = s1; s1 = s2; s2 = tmp; }
-            if (s1 > s_lo) s_lo = s1;
+            if (s1 > s_lo) { s_lo = s1; cross_axis = a; }
             if (s2 < s_hi) s_hi = s2;
         }
     }
+    const double dlen = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
     if (!(s_lo < s_hi)) return 0;
     int32_t iv[3];
     for (int a = 0; a < 3; ++a) {
@@ -214,6 +220,10 @@ int o_hull_entry(const o_cfg *g, const uint8_t *mask, const double T[3], const d
         int64_t j = iv[0] + (int64_t)n[0] * (iv[1] + (int64_t)n[1] * iv[2]);
         if (mask == NULL || mask[j]) {
             *s_hit = s_cur;
+            if (cond && cross_axis >= 0) {
+                double c = dlen / fabs(D[cross_axis]);
+                if (c > *cond) *cond = c;
+            }
             return 1;
         }
         double tm[3];
@@ -231,6 +241,8 @@ int o_hull_entry(const o_cfg *g, const uint8_t *mask, const double T[3], const d
         for (int a = 0; a < 3; ++a) {
             if (tm[a] == s_next) {
                 iv[a] += D[a] > 0.0 ? 1 : -1;
+                if (cross_axis < 0 || fabs(D[a]) < fabs(D[cross_axis]) || tm[cross_axis] != s_next)
+                    cross_axis = a;
             } else if (margin) {
                 double m = o_face_dist(T[a] + s_next * D[a], o[a], d[a]);
                 if (m < *margin) *margin = m;
@@ -248,7 +260,7 @@ int o_hull_entry(const o_cfg *g, const uint8_t *mask, const double T[3], const d
  *            theta_out, psi_out, phi, wepl.
  * st[0..11] = u_in, u_out, t0, th0, v0, ps0, t2, th2, v2, ps2, cos phi, sin phi. */
 static int o_state_one(const o_cfg *g, const uint8_t *mask, const double *const h[12], int64_t i,
-                       double st[12], double *margin)
+                       double st[12], double *margin, double *cond)
 {
     double c = cos(h[10][i]), s = sin(h[10][i]);
     double ua = h[0][i] * c + h[1][i] * s, ta = -h[0][i] * s + h[1][i] * c, va = h[2][i];
@@ -264,8 +276,8 @@ static int o_state_one(const o_cfg *g, const uint8_t *mask, const double *const 
     double To[3] = {h[3][i], h[4][i], h[5][i]};
     double Do[3] = {-(c - tto * s), -(s + tto * c), -tpo};
     double s_in, s_out;
-    if (!o_hull_entry(g, mask, Ti, Di, S, &s_in, margin)) return 0;
-    if (!o_hull_entry(g, mask, To, Do, S, &s_out, margin)) return 0;
+    if (!o_hull_entry(g, mask, Ti, Di, S, &s_in, margin, cond)) return 0;
+    if (!o_hull_entry(g, mask, To, Do, S, &s_out, margin, cond)) return 0;
     double u_in = ua + s_in, u_out = ub - s_out;
     if (!(u_out > u_in)) return 0;
     st[0] = u_in;
@@ -287,7 +299,7 @@ int o_prepare(const o_cfg *g, const uint8_t *mask, int64_t n, const double *cons
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
         double m = INFINITY;
-        valid[i] = o_state_one(g, mask, h, i, states + 12 * i, &m);
+        valid[i] = o_state_one(g, mask, h, i, states + 12 * i, &m, NULL);
         if (margin) margin[i] = m;
     }
     return 0;
@@ -357,7 +369,7 @@ int o_mlp_points(const o_cfg *g, const uint8_t *mask, int64_t n, const double *c
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i) {
         double st[12];
-        int ok = o_state_one(g, mask, h, i, st, NULL);
+        int ok = o_state_one(g, mask, h, i, st, NULL, NULL);
         npts[i] = (int32_t)o_polyline(g, st, ok, pts + (int64_t)3 * max_pts * i, max_pts, NULL);
     }
     return 0;
@@ -518,17 +530,17 @@ int o_rows(const o_cfg *g, const uint8_t *mask, int64_t n, const double *const h
 #pragma omp for schedule(dynamic, 64)
         for (int64_t i = 0; i < n; ++i) {
             double st[12];
-            double m = INFINITY;
-            int ok = o_state_one(g, mask, h, i, st, &m);
+            double m = INFINITY, cd = 1.0;
+            int ok = o_state_one(g, mask, h, i, st, &m, &cd);
             int64_t np = o_polyline(g, st, ok, pts, cap_pts, &m);
             if (np > cap_pts) {
                 cap_pts = np;
                 pts = (double *)realloc(pts, sizeof(double) * 3 * cap_pts);
                 m = INFINITY;
-                o_state_one(g, mask, h, i, st, &m);
+                cd = 1.0;
+                o_state_one(g, mask, h, i, st, &m, &cd);
                 np = o_polyline(g, st, ok, pts, cap_pts, &m);
             }
-            double cd = 1.0;
             if (out_j == NULL) {
                 rowptr[i + 1] = o_walk_row(g, mask, pts, np, NULL, NULL, 0, &m, &cd);
             } else {

@@ -612,3 +612,23 @@ def test_walk_consecutive_segments_share_their_vertex():
     ix = j % 40
     assert np.all(np.diff(ix) == 1), ix
     assert np.all(ln[1:-1] > 1.5)
+
+
+def test_hull_entry_conditioning_of_the_crossed_face():
+    # a line nearly parallel to the z faces entering the hull through one of
+    # them: conditioning |D| / |D_z| (how far a position error moves the
+    # crossing along the line); through an x face head on: about 1
+    shape = (20, 20, 10)
+    geo_z = _geo(shape=shape, origin=(-10.0, -10.0, -5.0),
+                 mask=(np.arange(10)[:, None, None] >= 5).repeat(20, 1).repeat(20, 2).astype(np.uint8))
+    D = np.array([1.0, 0.0, 0.02])
+    hit, s, m, c = O.hull_entry(geo_z, [-9.9, 0.1, -0.15], D, 30.0, with_cond=True)
+    assert hit and abs(s - 7.5) < 1e-12
+    assert abs(c - np.linalg.norm(D) / 0.02) < 1e-9
+    geo_x = _geo(shape=shape, origin=(-10.0, -10.0, -5.0),
+                 mask=(np.arange(20)[None, None, :] >= 12).repeat(10, 0).repeat(20, 1).astype(np.uint8))
+    hit, s, m, c = O.hull_entry(geo_x, [-9.9, 0.1, 0.15], D, 30.0, with_cond=True)
+    assert hit and abs(s - 11.9) < 1e-12 and abs(c - np.linalg.norm(D)) < 1e-12
+    # a line that starts inside its first hull voxel crosses no face: 1
+    hit, s, m, c = O.hull_entry(geo_x, [2.5, 0.1, 0.15], D, 30.0, with_cond=True)
+    assert hit and s == 0.0 and c == 1.0
