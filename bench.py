@@ -55,7 +55,7 @@ def _args():
     p.add_argument("--mode", default="fused", choices=["fused", "csr", "packed"],
                    help="row form: recomputed on the fly, or stored (built once, timed apart)")
     p.add_argument("--walk", default=None, choices=["rounds", "lanes"],
-                   help="walk of the fused DROP step (default: the library's, rounds)")
+                   help="walk of the fused DROP step (default: the library's, lanes)")
     p.add_argument("--chord", default="fixed16", choices=["fixed16", "fp16"],
                    help="chord code of the packed rows")
     p.add_argument("--cpu-sample", type=int, default=320000)
@@ -397,6 +397,11 @@ def run_ours(args):
     peaks = _measured_peaks()
     fp32_peak, atomic_peak = measured_ceilings(pct, local, cfg.n_vox)
     avg_launch_s = fused_ms * 1e-3 / max(timed_n, 1)
+    persistent = timed_n == 0 and args.mode == "fused"
+    if persistent:
+        # one persistent launch per solve: the average block step (walk,
+        # barriers and apply) from the step time
+        avg_launch_s = step_ms * 1e-3 / blocks_per_solve
     blocks_per_iter = math.ceil(n / block)
     flops_launch = fused_flops(valid, mean_pts, mean_nnz) / blocks_per_iter
     achieved = flops_launch / avg_launch_s / 1e12
@@ -406,7 +411,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp32_peak,
                 "traffic": (per_row_traffic * valid / blocks_per_iter) if per_row_traffic else None,
-                "kernel": "k_drop_rounds" if walk == pct.PCT_WALK_ROUNDS else "k_drop_fused",
+                "kernel": ("k_drop_batch (one persistent launch per solve; per block step incl. "
+                           "barriers and apply)") if persistent else
+                          ("k_drop_rounds" if walk == pct.PCT_WALK_ROUNDS else "k_drop_fused"),
                 "avg_launch_ms": avg_launch_s * 1e3,
                 "launches_timed": timed_n, "launches": fused_n,
                 "peak_source": "measured: pct_peak_fp32, FP32 FMA loop filling every SM (best of 5, "

@@ -110,7 +110,15 @@ enum pct_option {
      * the same rows; performance only.  Default PCT_WALK_LANES (on the torso
      * workload the round walk measured 1.20 ms per 320000-proton block step
      * against 1.03 ms). */
-    PCT_OPT_WALK = 12
+    PCT_OPT_WALK = 12,
+    /* pct_solve in PCT_MODE_FUSED with block_size <= this value runs all its
+     * block steps and applies in one persistent cooperative launch (the
+     * batched solve of pct_solve_batch with this context alone: no launch per
+     * block, bounded barrier waits; options of the batched solve apply, and
+     * its device errors and barrier timeouts are reported by pct_synchronize).
+     * 0 = never.  Default 32000.  Performance only; PCT_OPT_TIMING does not
+     * time the block steps of such a solve. */
+    PCT_OPT_PERSISTENT_BLOCK = 13
 };
 
 /* Walks of one proton's polyline by one warp (PCT_OPT_WALK). */

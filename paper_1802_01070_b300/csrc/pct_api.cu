@@ -99,6 +99,7 @@ struct pct_ctx {
     int64_t spin_limit = 1 << 27;
     int batch_cta = 0, batch_ctas = 0, batch_lanes = 32;
     int lanes_opt = 32;                  // lanes per proton of batched solves (PCT_OPT_BATCH_LANES)
+    int64_t persist_max = 32000;         // pct_solve: persistent launch up to this block size (PCT_OPT_PERSISTENT_BLOCK)
     int walk = kWalkLanes;               // walk of the DROP step and the row writer (PCT_OPT_WALK)
     int64_t graph_replays = 0;
     ScanDesc* d_scans = nullptr;
@@ -587,6 +588,10 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
     case PCT_OPT_AUTOTUNE:
         c->autotune = value ? 1 : 0;
         return PCT_OK;
+    case PCT_OPT_PERSISTENT_BLOCK:
+        if (value < 0) return fail(c, PCT_ERR_ARG, "negative persistent block size");
+        c->persist_max = value;
+        return PCT_OK;
     case PCT_OPT_WALK:
         if (value != PCT_WALK_LANES && value != PCT_WALK_ROUNDS) return fail(c, PCT_ERR_ARG, "unknown walk");
         c->walk = (int)value;
@@ -632,6 +637,7 @@ pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
     case PCT_OPT_AUTOTUNE: *value = c->autotune; return PCT_OK;
     case PCT_OPT_BATCH_LANES: *value = c->lanes_opt; return PCT_OK;
     case PCT_OPT_WALK: *value = c->walk; return PCT_OK;
+    case PCT_OPT_PERSISTENT_BLOCK: *value = c->persist_max; return PCT_OK;
     case PCT_OPT_SPIN_LIMIT: *value = c->spin_limit; return PCT_OK;
     case PCT_OPT_TEST_UNREACHABLE_BARRIER: *value = c->test_unreachable; return PCT_OK;
     default: return PCT_ERR_ARG;
@@ -827,6 +833,13 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
     pct_status s = need_histories(c);
     if (s != PCT_OK) return s;
     if (c->n == 0 || iters == 0) return PCT_OK;
+    if (c->mode == PCT_MODE_FUSED && c->persist_max > 0 && block_size <= c->persist_max && c->d_hist) {
+        // every block step of every iteration in one persistent cooperative
+        // launch: the batched solve with this scan alone (no launch per block)
+        pct_ctx* cs[1] = {c};
+        float* xs[1] = {x};
+        return pct_solve_batch(cs, 1, &iters, &lambda, &block_size, xs);
+    }
     if ((s = ensure_acc(c)) != PCT_OK) return s;
     if (c->mode == PCT_MODE_FUSED) {
         if ((s = prepare(c)) != PCT_OK) return s;
@@ -995,6 +1008,8 @@ pct_status pct_solve_regions(pct_ctx* c, int32_t n_regions, int32_t halo, int32_
         }
         pct_ctx* sub = g.sub;
         sub->cta = c->cta;
+        sub->walk = c->walk;
+        sub->persist_max = c->persist_max;
         sub->du_um = c->du_um;
         sub->kmax_floor = c->kmax;
         if ((s = build_sigma_table(sub)) != PCT_OK) {
