@@ -56,6 +56,9 @@ def _args():
                    help="row form: recomputed on the fly, or stored (built once, timed apart)")
     p.add_argument("--walk", default=None, choices=["rounds", "lanes"],
                    help="walk of the fused DROP step (default: the library's, lanes)")
+    p.add_argument("--persistent-block", type=int, default=None,
+                   help="largest block size solved in one persistent launch (0: never; default: the "
+                        "library's, 32000)")
     p.add_argument("--chord", default="fixed16", choices=["fixed16", "fp16"],
                    help="chord code of the packed rows")
     p.add_argument("--cpu-sample", type=int, default=320000)
@@ -320,6 +323,8 @@ def run_ours(args):
     if args.walk:
         ctx.set_option(pct.PCT_OPT_WALK, {"rounds": pct.PCT_WALK_ROUNDS, "lanes": pct.PCT_WALK_LANES}[args.walk])
     walk = ctx.get_option(pct.PCT_OPT_WALK)
+    if args.persistent_block is not None:
+        ctx.set_option(pct.PCT_OPT_PERSISTENT_BLOCK, args.persistent_block)
     ctx.load_histories(hist)
     build_s = None
     if mode != pct.PCT_MODE_FUSED:
