@@ -33,7 +33,18 @@ inputs differ between the two sides:
       CHORD_TOL_MM (for a row whose voxel sequence differs: the row's summed
       chord in j).  On a grazing crossing a chord can be correct by the row
       rule and still differ by more than CHORD_TOL_MM, which moves that
-      voxel's update.
+      voxel's update;
+  (c) residual (for one block step from a known iterate x, with the rows'
+      measurements b): voxel j's update takes lambda a_ij r_i / s_j from every
+      row i through it, and r_i = (b_i - a_i.x) / ||a_i||^2 depends on the whole
+      row.  A row that differs somewhere -- most of all one whose hull entry
+      point moved along a grazing tracker line, which shifts the whole path --
+      changes r_i on voxels where its chords agree.  Each side's r_i is
+      evaluated in FP64 from its own row and the same x; voxel j of row i is
+      left out when a_ij |r_i(GPU) - r_i(oracle)| > RESID_TOL (a tenth of the
+      RSP tolerance; lambda <= 1 <= s_j makes it a bound on the move).
+      Across several blocks x itself differs and (c) does not apply: such
+      runs are compared by statistics over all hull voxels.
 """
 from __future__ import annotations
 
@@ -44,6 +55,7 @@ MLP_TOL_MM = 1e-3       # MLP point tolerance
 CHORD_TOL_MM = 2e-3     # chord tolerance (difference of two MLP-derived crossings)
 POS_ERR_MM = 4e-5       # position error of the FP32 path: MLP points agree with the oracle's to
                         # 6.5e-6 mm on the small scans and 3.3e-5 mm on the full-size ones
+RESID_TOL = 1e-4        # largest move a_ij |delta r_i| of a voxel's update by a row's residual
 
 
 def chord_tol(cond):
@@ -109,14 +121,23 @@ class Exclusion:
     Feed consecutive chunks of rows (GPU padded rows and the oracle's CSR rows
     of the same protons) in proton order with ``add``; chunks may start and end
     anywhere, DROP blocks of ``block`` rows are closed as they complete.  Call
-    ``finish`` after the last chunk.
+    ``finish`` after the last chunk.  With ``x`` (the iterate of a single block
+    step) and ``b`` the residual part (c) is applied as well.
     """
 
-    def __init__(self, n_vox: int, block: int):
+    def __init__(self, n_vox: int, block: int, x=None, b=None):
         self.n_vox = int(n_vox)
         self.block = int(block)
         self.count = np.zeros(self.n_vox, dtype=bool)
         self.chord = np.zeros(self.n_vox, dtype=bool)
+        self.resid = np.zeros(self.n_vox, dtype=bool)
+        self.rows_resid = 0
+        # part (c): the iterate the block step starts from and the rows'
+        # measurements (indexed by row, from the first row fed)
+        self.x = None if x is None else np.asarray(x, dtype=np.float64).reshape(-1)
+        self.b = None if b is None else np.asarray(b, dtype=np.float64).reshape(-1)
+        if (self.x is None) != (self.b is None):
+            raise ValueError("the residual part needs both x and b")
         self.unexcused = []
         self.seq_diff = 0
         self.rows = 0
@@ -147,6 +168,8 @@ class Exclusion:
         g_rows = np.broadcast_to(np.arange(m)[:, None], (m, W))[keep]
         g_j = gidx[keep].astype(np.int64)
         o_rows = np.repeat(np.arange(m), np.diff(rowptr))
+        if self.x is not None:
+            self._residual(first_row, gidx, glen, keep, g_rows, rowptr, j, ln, o_rows)
         key = np.unique(o_rows.astype(np.int64) * self.n_vox + j.astype(np.int64))
         ko_rows, ko_j = key // self.n_vox, key % self.n_vox
         for b in np.unique(blk):
@@ -161,6 +184,27 @@ class Exclusion:
             om = (ko_rows >= lo) & (ko_rows < hi)
             self._co += np.bincount(ko_j[om], minlength=self.n_vox)
 
+    def _residual(self, first_row, gidx, glen, keep, g_rows, rowptr, j, ln, o_rows):
+        m = gidx.shape[0]
+        x = self.x
+        b = self.b[first_row:first_row + m]
+        g_j = gidx[keep].astype(np.int64)
+        g_l = np.asarray(glen, dtype=np.float64)[keep]
+        o_j = np.asarray(j).astype(np.int64)
+        o_l = np.asarray(ln, dtype=np.float64)
+
+        def resid(rows, jj, ll):
+            s = np.bincount(rows, weights=ll * x[jj], minlength=m)
+            q = np.bincount(rows, weights=ll * ll, minlength=m)
+            return np.where(q > 0, (b - s) / np.where(q > 0, q, 1.0), 0.0)
+
+        dr = np.abs(resid(g_rows, g_j, g_l) - resid(o_rows, o_j, o_l))
+        hit_g = g_l * dr[g_rows] > RESID_TOL
+        hit_o = o_l * dr[o_rows] > RESID_TOL
+        self.resid[g_j[hit_g]] = True
+        self.resid[o_j[hit_o]] = True
+        self.rows_resid += int(np.union1d(g_rows[hit_g], o_rows[hit_o]).size)
+
     def finish(self):
         self._close()
         self._blk = -1
@@ -168,7 +212,7 @@ class Exclusion:
 
     @property
     def mask(self):
-        return self.count | self.chord
+        return self.count | self.chord | self.resid
 
 
 def solve_parity(xg, xo, hull, excluded):
@@ -192,6 +236,9 @@ def solve_parity(xg, xo, hull, excluded):
     if isinstance(excluded, Exclusion):
         out["excluded_count"] = int((hm & excluded.count).sum())
         out["excluded_chord_only"] = int((hm & excluded.chord & ~excluded.count).sum())
+        if excluded.x is not None:
+            out["excluded_resid_only"] = int((hm & excluded.resid & ~excluded.count & ~excluded.chord).sum())
+            out["rows_resid"] = excluded.rows_resid
         out["rows"] = excluded.rows
         out["rows_seq_diff"] = excluded.seq_diff
         out["rows_unexcused"] = len(excluded.unexcused)

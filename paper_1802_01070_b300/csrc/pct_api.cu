@@ -874,7 +874,7 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP kernel");
             ++c->fused_launches;
             if (e1) cudaEventRecord(e1, c->stream);
-            e = launch_drop_apply(L, c->n_vox, x, c->d_acc, lambda, c->d_next);
+            e = launch_drop_apply(L, c->n_vox, c->d_mask, x, c->d_acc, lambda, c->d_next);
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP apply kernel");
         }
     }

@@ -82,9 +82,10 @@ cudaError_t launch_compact(const Launch& L, const float* rec, int64_t stride, in
 cudaError_t launch_drop_fused(const Launch& L, const Geo& G, const float* rec, int64_t stride,
                               const int64_t* vidx, const int64_t* boff, int64_t k, int64_t count,
                               const float* x, float2* acc, unsigned long long* next);
-// Block apply; resets the work counter `next` when not null.
-cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda,
-                              unsigned long long* next);
+// Block apply over the hull voxels (mask != 0); resets the work counter
+// `next` when not null.
+cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, const uint8_t* mask, float* x, float2* acc,
+                              float lambda, unsigned long long* next);
 
 // data cleaning (pct_clean.cu): bins of (gantry angle, t, v) and the cut
 struct CleanBins {

@@ -520,12 +520,15 @@ k_rows_rounds(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, un
 // voxel j, and clear the accumulator for the next block.
 // `next` (if not null): the work counter of the block step, reset here for
 // the next block step on the stream.
-__global__ void k_drop_apply(int64_t n_vox, float* __restrict__ x, float2* __restrict__ acc,
-                             float lambda, unsigned long long* next)
+__global__ void k_drop_apply(int64_t n_vox, const uint8_t* __restrict__ mask, float* __restrict__ x,
+                             float2* __restrict__ acc, float lambda, unsigned long long* next)
 {
     if (next && blockIdx.x == 0 && threadIdx.x == 0) *next = 0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_vox; j += stride) {
+        // only hull voxels are ever scattered into: the accumulator of the
+        // others is not read (whole 32-byte sectors of it are skipped)
+        if (!__ldg(mask + j)) continue;
         const float2 a = acc[j];
         if (a.y > 0.f) {
             x[j] = fmaf(lambda, a.x / a.y, x[j]);
@@ -824,13 +827,13 @@ cudaError_t launch_compact(const Launch& L, const float* rec, int64_t stride, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, float* x, float2* acc, float lambda,
-                              unsigned long long* next)
+cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, const uint8_t* mask, float* x, float2* acc,
+                              float lambda, unsigned long long* next)
 {
     if (n_vox <= 0) return cudaSuccess;
     int64_t blocks = (n_vox + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
-    k_drop_apply<<<(unsigned)blocks, 256, 0, L.stream>>>(n_vox, x, acc, lambda, next);
+    k_drop_apply<<<(unsigned)blocks, 256, 0, L.stream>>>(n_vox, mask, x, acc, lambda, next);
     PCT_LAUNCH_TAIL(L);
 }
 

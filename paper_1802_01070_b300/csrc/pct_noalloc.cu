@@ -217,7 +217,7 @@ extern "C" pct_status pct_solve_noalloc(const pct_grid* grid, const uint8_t* hul
                 if ((e = launch_drop_fused(L, geo, S.rec, stride, S.vidx, S.boff, first / block_size, count, x,
                                            S.acc, S.next)) != cudaSuccess)
                     return cuda_fail(e, "DROP kernel");
-                if ((e = launch_drop_apply(L, n_vox, x, S.acc, lambda, S.next)) != cudaSuccess)
+                if ((e = launch_drop_apply(L, n_vox, hull_mask, x, S.acc, lambda, S.next)) != cudaSuccess)
                     return cuda_fail(e, "DROP apply kernel");
             }
         }

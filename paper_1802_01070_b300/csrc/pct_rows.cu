@@ -465,6 +465,11 @@ __device__ __forceinline__ void unpack32(const uint8_t* __restrict__ codes,
     j = inside ? g.index(ix, iy, iz) : 0;
 }
 
+// Chunks of 32 entries of a packed row that the DROP step decodes once and
+// keeps in registers for the scatter (a torso row has ~224 entries); the
+// entries beyond them are decoded again for the scatter.
+constexpr int kPackedKeep = 8;
+
 __global__ void __launch_bounds__(kRowCta)
 k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, const short4* __restrict__ start,
               const uint8_t* __restrict__ codes, const uint16_t* __restrict__ lens, float unit,
@@ -483,9 +488,43 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
     const Dims g{gc.nx, gc.ny, gc.nz};
     const int nvox = gc.nx * gc.ny * gc.nz;
     const short4 s0 = start[i];
-    float s = 0.f, q = 0.f;
+    const int64_t nchunk = (e1 - a + kWarp - 1) / kWarp;
     int bx = s0.x, by = s0.y, bz = s0.z;
-    for (int64_t e0 = a; e0 < e1; e0 += kWarp) {
+    // the kept chunks: decode all, then gather x, then accumulate in entry order
+    int jk[kPackedKeep];
+    float lk[kPackedKeep], xk[kPackedKeep];
+#pragma unroll
+    for (int c = 0; c < kPackedKeep; ++c) {
+        jk[c] = -1;
+        lk[c] = 0.f;
+        if (c < nchunk) {   // warp-uniform
+            int j;
+            float l;
+            bool in;
+            unpack32(codes, lens, unit, a + c * kWarp, e1, bx, by, bz, g, j, l, in);
+            if (in && (unsigned)j >= (unsigned)nvox) {
+                atomicOr(flags, kFlagRowBounds);
+                in = false;
+            }
+            if (in) {
+                jk[c] = j;
+                lk[c] = l;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kPackedKeep; ++c) xk[c] = jk[c] >= 0 ? __ldg(x + jk[c]) : 0.f;
+    float s = 0.f, q = 0.f;
+#pragma unroll
+    for (int c = 0; c < kPackedKeep; ++c) {
+        if (jk[c] >= 0) {
+            s = fmaf(lk[c], xk[c], s);
+            q = fmaf(lk[c], lk[c], q);
+        }
+    }
+    // the rest of a long row
+    const int kx = bx, ky = by, kz = bz;
+    for (int64_t e0 = a + kPackedKeep * kWarp; e0 < e1; e0 += kWarp) {
         int j;
         float l;
         bool in;
@@ -506,10 +545,13 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
     }
     if (!(q > 0.f)) return;
     const float r = (__ldg(b + i) - s) / q;
-    bx = s0.x;
-    by = s0.y;
-    bz = s0.z;
-    for (int64_t e0 = a; e0 < e1; e0 += kWarp) {
+#pragma unroll
+    for (int c = 0; c < kPackedKeep; ++c)
+        if (jk[c] >= 0) atomicAdd(acc + jk[c], make_float2(lk[c] * r, 1.f));
+    bx = kx;
+    by = ky;
+    bz = kz;
+    for (int64_t e0 = a + kPackedKeep * kWarp; e0 < e1; e0 += kWarp) {
         int j;
         float l;
         bool in;

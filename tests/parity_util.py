@@ -82,13 +82,15 @@ def compare_rows(gidx, glen, gnnz, rowptr, j, ln, margin, cond=None, dL=None,
     return n, excused, worst, bad
 
 
-def gpu_exclusion(ctx, rowptr, j, ln, margin, cond, block, first=0, count=None, chunk=8192):
+def gpu_exclusion(ctx, rowptr, j, ln, margin, cond, block, first=0, count=None, chunk=8192, x=None, b=None):
     """The voxels the comparison rule of ``oracle.compare`` leaves out, for the
     protons [first, first + count) loaded in ``ctx`` against the oracle's CSR
     rows of the same protons (rowptr indexed from ``first``), DROP blocks of
-    ``block`` rows counted from ``first``."""
+    ``block`` rows counted from ``first``.  For a single block step from the
+    iterate ``x`` with measurements ``b`` (of those protons) the residual part
+    of the rule applies too."""
     n = ctx.n - first if count is None else count
-    ex = Exclusion(ctx.n_vox, block)
+    ex = Exclusion(ctx.n_vox, block, x=x, b=b)
     for a in range(0, n, chunk):
         k = min(n, a + chunk) - a
         _, _, nnz = ctx.rows(first + a, k, max_nnz=0)

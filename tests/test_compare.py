@@ -3,11 +3,13 @@
 Checks that identical rows exclude nothing, that a chord difference beyond
 tolerance excludes its voxel only on an oracle-flagged (near-face) row and is
 reported as an unexcused disagreement otherwise, that the tolerance grows with
-the row's crossing conditioning, and that DROP counts are compared per block.
+the row's crossing conditioning, that DROP counts are compared per block, and
+that a row whose residual moved excludes its voxels in a single block step.
 """
 import numpy as np
 
-from oracle.compare import NEAR_FACE_MM, Exclusion, chord_tol, compare_row_chunk, near_face, solve_parity
+from oracle.compare import (NEAR_FACE_MM, RESID_TOL, Exclusion, chord_tol, compare_row_chunk, near_face,
+                            solve_parity)
 
 
 def _rows():
@@ -89,3 +91,38 @@ def test_sequence_difference_and_block_counts():
     hull = np.ones(10, bool)
     p = solve_parity(xg, xo, hull, ex)
     assert p["clean_max"] == 0.0 and p["excluded"] == 1 and p["all_max"] == 0.5
+
+
+def test_residual_part_excludes_the_voxels_of_a_row_whose_residual_moved():
+    # row 0 of the oracle: voxels 1, 2, 3; on the GPU its hull entry moved along
+    # a grazing tracker line, so the first chord is 0.5 mm shorter while the far
+    # chords agree exactly.  Its residual r_0 = (b - a.x) / ||a||^2 differs, and
+    # with it the update of voxels 2 and 3, where nothing else differs.
+    rowptr, j, ln = _rows()
+    gi, gl, nnz = _pad(rowptr, j, ln)
+    gl[0, 0] -= 0.5
+    margin, cond = np.zeros(3), np.ones(3)     # flagged: the row differs legitimately
+    x = np.ones(10)
+    b = np.array([2.5, 1.5, 2.2])
+    ex = Exclusion(10, 3)
+    ex.add(0, gi, gl, nnz, rowptr, j, ln, margin, cond)
+    ex.finish()
+    assert np.nonzero(ex.mask)[0].tolist() == [1]           # by chord only
+    exr = Exclusion(10, 3, x=x, b=b)
+    exr.add(0, gi, gl, nnz, rowptr, j, ln, margin, cond)
+    exr.finish()
+    assert np.nonzero(exr.mask)[0].tolist() == [1, 2, 3] and exr.rows_resid == 1
+    # by hand: r = (2.5 - 2.2) / 1.74 on the oracle's row, (2.5 - 1.7) / 0.74 on
+    # the GPU's; a chord of 0.5 mm times that difference is far above RESID_TOL
+    r_o = (2.5 - 2.2) / (1.0 + 0.25 + 0.49)
+    r_g = (2.5 - 1.7) / (0.25 + 0.25 + 0.49)
+    assert 0.5 * abs(r_g - r_o) > RESID_TOL
+    # a compensating chord shift between two voxels of equal x leaves r unchanged:
+    # only the chord part excludes them
+    gi, gl, nnz = _pad(rowptr, j, ln)
+    gl[1, 0] += 0.01
+    gl[1, 1] -= 0.01
+    exr = Exclusion(10, 3, x=x, b=b)
+    exr.add(0, gi, gl, nnz, rowptr, j, ln, margin, cond)
+    exr.finish()
+    assert exr.rows_resid == 0 and np.nonzero(exr.mask)[0].tolist() == [4, 5]

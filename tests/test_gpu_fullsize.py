@@ -90,7 +90,11 @@ def _free_running(cfg, hull, sub, iters, block, label, oracle=None):
         c1.solve(x, iters, cfg.lam, block)
         c1.synchronize()
         xg = x.cpu().numpy().astype(np.float64)
-        ex = U.gpu_exclusion(c1, rowptr, j, ln, margin, cond, block)
+        # one block step from x0: the residual part of the rule applies
+        single = iters == 1 and sub_np["wepl"].size <= block
+        ex = U.gpu_exclusion(c1, rowptr, j, ln, margin, cond, block,
+                             x=hull.astype(np.float64) if single else None,
+                             b=sub_np["wepl"] if single else None)
     A = O.csr(rowptr, j, ln, geo.n_vox)
     xo = O.drop(A, sub_np["wepl"].astype(np.float64), iters, cfg.lam, block, hull.astype(np.float64))
     del A
@@ -120,7 +124,8 @@ def _teacher_forced(cfg, hull, sub, oracle, block, x_start, label):
             ck.synchronize()
             rp = rowptr[a:a + k + 1] - rowptr[a]
             e0, e1 = int(rowptr[a]), int(rowptr[a + k])
-            ex = U.gpu_exclusion(ck, rp, j[e0:e1], ln[e0:e1], margin[a:a + k], cond[a:a + k], block)
+            ex = U.gpu_exclusion(ck, rp, j[e0:e1], ln[e0:e1], margin[a:a + k], cond[a:a + k], block,
+                                 x=xb, b=sub_np["wepl"][a:a + k])
             A = O.csr(rp, j[e0:e1], ln[e0:e1], geo.n_vox)
             xo = O.drop(A, sub_np["wepl"][a:a + k].astype(np.float64), 1, cfg.lam, block, xb)
             r = U.solve_parity(x.cpu().numpy(), xo, hull, ex)
@@ -143,7 +148,8 @@ def test_torso_full_size():
     torch.cuda.empty_cache()
     r, _ = _free_running(cfg, hull, sub, 1, B, "torso, one block of %d, 1 iteration" % B)
     assert r["clean_max"] <= 1e-3 and r["frac_within_1e-3"] >= 0.999
-    assert r["excluded"] <= 0.01 * hull.sum()
+    # the rule rests on rare rows: few whose residual moved, few voxels left out
+    assert r["rows_resid"] <= 0.002 * r["rows"] and r["excluded"] <= 0.03 * hull.sum()
 
 
 def test_torso_eight_blocks_six_iterations():
