@@ -58,7 +58,7 @@ def _args():
                    help="walk of the fused DROP step (default: the library's, lanes)")
     p.add_argument("--persistent-block", type=int, default=None,
                    help="largest block size solved in one persistent launch (0: never; default: the "
-                        "library's, 32000)")
+                        "library's, 0)")
     p.add_argument("--chord", default="fixed16", choices=["fixed16", "fp16"],
                    help="chord code of the packed rows")
     p.add_argument("--cpu-sample", type=int, default=320000)

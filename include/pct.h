@@ -116,7 +116,10 @@ enum pct_option {
      * batched solve of pct_solve_batch with this context alone: no launch per
      * block, bounded barrier waits; options of the batched solve apply, and
      * its device errors and barrier timeouts are reported by pct_synchronize).
-     * 0 = never.  Default 32000.  Performance only; PCT_OPT_TIMING does not
+     * 0 = never.  Default 0: on the head workload (1e7 protons, block 3200)
+     * a block step measured 27.2 us this way against 24.8 us with a launch of
+     * the block kernel and one of the apply, so it pays only when several
+     * scans share the GPU (pct_solve_batch).  Performance only; PCT_OPT_TIMING does not
      * time the block steps of such a solve. */
     PCT_OPT_PERSISTENT_BLOCK = 13
 };

@@ -41,8 +41,9 @@ inputs differ between the two sides:
       point moved along a grazing tracker line, which shifts the whole path --
       changes r_i on voxels where its chords agree.  Each side's r_i is
       evaluated in FP64 from its own row and the same x; voxel j of row i is
-      left out when a_ij |r_i(GPU) - r_i(oracle)| > RESID_TOL (a tenth of the
-      RSP tolerance; lambda <= 1 <= s_j makes it a bound on the move).
+      left out when a_ij |r_i(GPU) - r_i(oracle)| > RESID_TOL |x_j| (a tenth
+      of the relative RSP tolerance; lambda <= 1 <= s_j makes it a bound on
+      the move).
       Across several blocks x itself differs and (c) does not apply: such
       runs are compared by statistics over all hull voxels.
 """
@@ -55,7 +56,7 @@ MLP_TOL_MM = 1e-3       # MLP point tolerance
 CHORD_TOL_MM = 2e-3     # chord tolerance (difference of two MLP-derived crossings)
 POS_ERR_MM = 4e-5       # position error of the FP32 path: MLP points agree with the oracle's to
                         # 6.5e-6 mm on the small scans and 3.3e-5 mm on the full-size ones
-RESID_TOL = 1e-4        # largest move a_ij |delta r_i| of a voxel's update by a row's residual
+RESID_TOL = 1e-4        # largest relative move a_ij |delta r_i| / |x_j| of a voxel by a row's residual
 
 
 def chord_tol(cond):
@@ -199,8 +200,8 @@ class Exclusion:
             return np.where(q > 0, (b - s) / np.where(q > 0, q, 1.0), 0.0)
 
         dr = np.abs(resid(g_rows, g_j, g_l) - resid(o_rows, o_j, o_l))
-        hit_g = g_l * dr[g_rows] > RESID_TOL
-        hit_o = o_l * dr[o_rows] > RESID_TOL
+        hit_g = g_l * dr[g_rows] > RESID_TOL * np.abs(x[g_j])
+        hit_o = o_l * dr[o_rows] > RESID_TOL * np.abs(x[o_j])
         self.resid[g_j[hit_g]] = True
         self.resid[o_j[hit_o]] = True
         self.rows_resid += int(np.union1d(g_rows[hit_g], o_rows[hit_o]).size)

@@ -99,7 +99,7 @@ struct pct_ctx {
     int64_t spin_limit = 1 << 27;
     int batch_cta = 0, batch_ctas = 0, batch_lanes = 32;
     int lanes_opt = 32;                  // lanes per proton of batched solves (PCT_OPT_BATCH_LANES)
-    int64_t persist_max = 32000;         // pct_solve: persistent launch up to this block size (PCT_OPT_PERSISTENT_BLOCK)
+    int64_t persist_max = 0;             // pct_solve: persistent launch up to this block size (PCT_OPT_PERSISTENT_BLOCK)
     int walk = kWalkLanes;               // walk of the DROP step and the row writer (PCT_OPT_WALK)
     int64_t graph_replays = 0;
     ScanDesc* d_scans = nullptr;

@@ -128,7 +128,6 @@ k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int
             // the next one (ordered before it by the barrier below)
             if (tid_in_scan == 0) atomicExch(d.next, 0ull);
             for (int64_t j = tid_in_scan; j < d.n_vox; j += nthr) {
-                if (!__ldg(d.mask + j)) continue;   // never scattered into
                 const float2 a = __ldcg(d.acc + j);
                 if (a.y > 0.f) {
                     __stcg(d.x + j, fmaf(d.lambda, a.x / a.y, __ldcg(d.x + j)));

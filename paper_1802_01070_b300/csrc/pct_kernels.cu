@@ -520,15 +520,53 @@ k_rows_rounds(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, un
 // voxel j, and clear the accumulator for the next block.
 // `next` (if not null): the work counter of the block step, reset here for
 // the next block step on the stream.
-__global__ void k_drop_apply(int64_t n_vox, const uint8_t* __restrict__ mask, float* __restrict__ x,
-                             float2* __restrict__ acc, float lambda, unsigned long long* next)
+// Block apply, 4 voxels per group: the hull bytes of two groups are read
+// first, then the accumulator and x of the groups that hold a hull voxel (the
+// others are never scattered into, and whole 32-byte sectors of their
+// accumulator are skipped).  x must be 16-byte aligned; k_drop_apply takes
+// the voxels from 4 * n4 on, and every voxel when x is not aligned.
+__device__ __forceinline__ void apply_group(uchar4 m, float4* __restrict__ x4, float4* __restrict__ acc4,
+                                            int64_t g, float lambda)
+{
+    float4 a01 = acc4[2 * g], a23 = acc4[2 * g + 1];
+    if (!((m.x && a01.y > 0.f) || (m.y && a01.w > 0.f) || (m.z && a23.y > 0.f) || (m.w && a23.w > 0.f)))
+        return;
+    float4 xv = x4[g];
+    if (m.x && a01.y > 0.f) { xv.x = fmaf(lambda, a01.x / a01.y, xv.x); a01.x = a01.y = 0.f; }
+    if (m.y && a01.w > 0.f) { xv.y = fmaf(lambda, a01.z / a01.w, xv.y); a01.z = a01.w = 0.f; }
+    if (m.z && a23.y > 0.f) { xv.z = fmaf(lambda, a23.x / a23.y, xv.z); a23.x = a23.y = 0.f; }
+    if (m.w && a23.w > 0.f) { xv.w = fmaf(lambda, a23.z / a23.w, xv.w); a23.z = a23.w = 0.f; }
+    x4[g] = xv;
+    acc4[2 * g] = a01;
+    acc4[2 * g + 1] = a23;
+}
+
+__global__ void k_drop_apply4(int64_t n4, const uchar4* __restrict__ mask4, float4* __restrict__ x4,
+                              float4* __restrict__ acc4, float lambda, unsigned long long* next)
 {
     if (next && blockIdx.x == 0 && threadIdx.x == 0) *next = 0ull;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_vox; j += stride) {
-        // only hull voxels are ever scattered into: the accumulator of the
-        // others is not read (whole 32-byte sectors of it are skipped)
-        if (!__ldg(mask + j)) continue;
+    int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    for (; g + stride < n4; g += 2 * stride) {
+        const uchar4 m0 = __ldg(mask4 + g), m1 = __ldg(mask4 + g + stride);
+        const bool h0 = m0.x | m0.y | m0.z | m0.w, h1 = m1.x | m1.y | m1.z | m1.w;
+        if (h0) apply_group(m0, x4, acc4, g, lambda);
+        if (h1) apply_group(m1, x4, acc4, g + stride, lambda);
+    }
+    if (g < n4) {
+        const uchar4 m0 = __ldg(mask4 + g);
+        if (m0.x | m0.y | m0.z | m0.w) apply_group(m0, x4, acc4, g, lambda);
+    }
+}
+
+__global__ void k_drop_apply(int64_t first, int64_t n_vox, const uint8_t* __restrict__ mask,
+                             float* __restrict__ x, float2* __restrict__ acc, float lambda,
+                             unsigned long long* next)
+{
+    if (next && blockIdx.x == 0 && threadIdx.x == 0) *next = 0ull;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = first + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n_vox; j += stride) {
+        if (!__ldg(mask + j)) continue;   // never scattered into
         const float2 a = acc[j];
         if (a.y > 0.f) {
             x[j] = fmaf(lambda, a.x / a.y, x[j]);
@@ -831,9 +869,24 @@ cudaError_t launch_drop_apply(const Launch& L, int64_t n_vox, const uint8_t* mas
                               float lambda, unsigned long long* next)
 {
     if (n_vox <= 0) return cudaSuccess;
-    int64_t blocks = (n_vox + 255) / 256;
+    // the mask and the accumulator are the library's own allocations
+    // (256-byte aligned); x is the caller's
+    const bool vec = ((uintptr_t)x & 15u) == 0 && ((uintptr_t)mask & 3u) == 0 && ((uintptr_t)acc & 15u) == 0;
+    const int64_t n4 = vec ? n_vox / 4 : 0;
+    if (n4 > 0) {
+        int64_t blocks = (n4 + 255) / 256;
+        if (blocks > 148 * 8) blocks = 148 * 8;
+        k_drop_apply4<<<(unsigned)blocks, 256, 0, L.stream>>>(n4, (const uchar4*)mask, (float4*)x, (float4*)acc,
+                                                              lambda, next);
+        ++*L.launches;
+        if (cudaError_t e = cudaGetLastError()) return e;
+        if (4 * n4 == n_vox) return cudaSuccess;
+        next = nullptr;
+    }
+    const int64_t rest = n_vox - 4 * n4;
+    int64_t blocks = (rest + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
-    k_drop_apply<<<(unsigned)blocks, 256, 0, L.stream>>>(n_vox, mask, x, acc, lambda, next);
+    k_drop_apply<<<(unsigned)blocks, 256, 0, L.stream>>>(4 * n4, n_vox, mask, x, acc, lambda, next);
     PCT_LAUNCH_TAIL(L);
 }
 

@@ -1,9 +1,8 @@
 // pct_round.cuh -- one warp per proton, the row of A built round by round:
 // in round r, lane l owns polyline segment 32 r + l + 1 (its MLP end point,
 // its voxel walk), so every lane does the same work.  Each lane walks its
-// segment with at most four predicated DDA steps, as many as the warp's
-// longest segment needs (the arithmetic of the walk in pct_warp.cuh, step for
-// step), giving up to kPieces pieces (voxel,
+// segment with a fixed number of predicated DDA steps (the arithmetic of the
+// walk in pct_warp.cuh, step for step), giving up to kPieces pieces (voxel,
 // chord); pieces that continue across segment ends are joined by a warp
 // segmented scan, and the finished runs (maximal visits of one voxel) are
 // appended in path order to a per-warp run list in shared memory.  The row
@@ -33,10 +32,8 @@ struct Piece {
     float l;
 };
 
-// Walk the segment A -> B (grid units) with at most kPieces - 1 predicated DDA
-// steps, fewer when no lane of the warp needs more (every lane of the warp
-// calls it; an idle lane passes A = B).  Returns the number of pieces;
-// *more = the segment needs more steps.
+// Walk the segment A -> B (grid units) with kPieces - 1 predicated DDA steps.
+// Returns the number of pieces; *more = the segment needs more steps.
 __device__ __forceinline__ int segment_pieces(const GridC& g, float ax, float ay, float az, float bx, float by,
                                               float bz, Piece (&pc)[kPieces], bool* more)
 {
@@ -62,7 +59,6 @@ __device__ __forceinline__ int segment_pieces(const GridC& g, float ax, float ay
     for (int k = 0; k < kPieces - 1; ++k) {
         const float tn = fminf(tmx, fminf(tmy, tmz));
         const bool cross = open && tn < 1.f;
-        if (!__any_sync(0xffffffffu, cross)) break;
         const float tc = fmaxf(tn, t);
         const int j = in_grid(g, ix, iy, iz) ? lin(g, ix, iy, iz) : -1;
         if (cross) {
@@ -121,30 +117,22 @@ __device__ __forceinline__ bool round_runs(const Path& P, const MlpC& mc, const 
         caz = __shfl_sync(full, bz, kWarp - 1);
         Piece pc[kPieces];
         bool more = false;
-        if (!act) {
-            bx = ax;
-            by = ay;
-            bz = az;
-        }
-        int np = segment_pieces(g, ax, ay, az, bx, by, bz, pc, &more);
-        if (!act) np = 0;
+        int np = 0;
+        if (act) np = segment_pieces(g, ax, ay, az, bx, by, bz, pc, &more);
         if (__any_sync(full, more)) {
             ok = false;
             break;
         }
-        const int maxnp = __reduce_max_sync(full, (unsigned)np);
         // does this lane's first piece continue the previous segment's last?
         const int first_j = act ? pc[0].j : 0;
         int last_j = 0;
         float last_l = 0.f;
 #pragma unroll
-        for (int k = 0; k < kPieces; ++k) {
-            if (k >= maxnp) break;
+        for (int k = 0; k < kPieces; ++k)
             if (k == np - 1) {
                 last_j = pc[k].j;
                 last_l = pc[k].l;
             }
-        }
         int prev_j = __shfl_up_sync(full, last_j, 1);
         bool prev_act = __shfl_up_sync(full, (int)act, 1) != 0;
         if (lane == 0) {
@@ -179,7 +167,6 @@ __device__ __forceinline__ bool round_runs(const Path& P, const MlpC& mc, const 
         int cnt = emit_open ? 1 : 0;
 #pragma unroll
         for (int k = 0; k < kPieces; ++k) {
-            if (k >= maxnp) break;
             if (k < np && !(k == np - 1 && cont)) {
                 const float l = k == 0 && m ? pc[k].l + carry : pc[k].l;
                 cnt += l > 0.f ? 1 : 0;
@@ -204,7 +191,6 @@ __device__ __forceinline__ bool round_runs(const Path& P, const MlpC& mc, const 
         }
 #pragma unroll
         for (int k = 0; k < kPieces; ++k) {
-            if (k >= maxnp) break;
             if (k < np && !(k == np - 1 && cont)) {
                 const float l = k == 0 && m ? pc[k].l + carry : pc[k].l;
                 if (l > 0.f) {

@@ -48,6 +48,7 @@ def test_sampled_launch_timing(cuda_device):
     ctx = pct.Context(cfg.shape, cfg.voxel, cfg.origin, hull=hull)
     ctx.load_histories({k: torch.from_numpy(v).cuda() for k, v in hist.items()})
     x = torch.from_numpy(hull.astype(np.float32)).cuda()
+    ctx.set_option(pct.PCT_OPT_PERSISTENT_BLOCK, 0)   # a launch per block step, each one timed
     with pytest.raises(pct.PctError) as e:
         ctx.set_option(pct.PCT_OPT_TIMING, -1)
     assert e.value.status == pct.PCT_ERR_ARG

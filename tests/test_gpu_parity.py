@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import oracle as O
+import paper_1802_01070_b300 as pct
 import synth
 from tests import parity_util as U
 
@@ -110,9 +111,12 @@ def test_adjoint_matches_oracle_and_identity(tiny):
     assert abs(lhs - rhs) <= 1e-5 * (np.abs(ax) @ np.abs(yv) + 1.0)
 
 
+@pytest.mark.parametrize("persistent", [0, 3200])
 @pytest.mark.parametrize("lam", [1e-4, 0.5])
-def test_drop_solve_matches_oracle(tiny, lam):
-    """Final RSP after 6 iterations at block size 3200 (ragged last block).
+def test_drop_solve_matches_oracle(tiny, lam, persistent):
+    """Final RSP after 6 iterations at block size 3200 (ragged last block), with
+    a launch per block step and (persistent = 3200) with all block steps in one
+    persistent launch.
 
     Every hull voxel that the comparison rule keeps (its DROP count s_j is the
     same on both sides in every block, and no oracle-flagged near-face row
@@ -123,8 +127,16 @@ def test_drop_solve_matches_oracle(tiny, lam):
     cfg, ctx, hull = tiny["cfg"], tiny["ctx"], tiny["hull"]
     x0 = hull.astype(np.float32)
     x = torch.from_numpy(x0).cuda()
-    ctx.solve(x, cfg.iters, lam, cfg.block)
-    ctx.synchronize()
+    ctx.set_option(pct.PCT_OPT_PERSISTENT_BLOCK, persistent)
+    try:
+        launches = ctx.stat(pct.PCT_STAT_LAUNCHES)
+        ctx.solve(x, cfg.iters, lam, cfg.block)
+        ctx.synchronize()
+        if persistent:
+            # one launch for the whole solve (plus the block lists built once)
+            assert ctx.stat(pct.PCT_STAT_LAUNCHES) - launches <= 4
+    finally:
+        ctx.set_option(pct.PCT_OPT_PERSISTENT_BLOCK, 0)
     xg = x.cpu().numpy().astype(np.float64)
     xo = O.drop(tiny["A"], tiny["hist"]["wepl"].astype(np.float64), cfg.iters, lam, cfg.block,
                 x0.astype(np.float64))
