@@ -20,8 +20,11 @@ constexpr int kRunSlotsRows = 24;
 constexpr int kScanCta = 1024;
 constexpr int kScanPer = 8;                      // elements per thread
 constexpr int kScanChunk = kScanCta * kScanPer;  // elements per CTA
-constexpr uint8_t kCodeStart = 13;               // step (0, 0, 0): the row's first run
-constexpr uint8_t kCodeInside = 32;              // bit: the entry's voxel is in the hull
+// Step code of a packed entry: bits 0-1, 2-3 and 4-5 hold the step + 1
+// (0, 1 or 2) along x, y and z; bit 6 is set when the entry's voxel is in the
+// hull.
+constexpr uint8_t kCodeStart = 1 | (1 << 2) | (1 << 4);   // step (0, 0, 0): the row's first run
+constexpr uint8_t kCodeInside = 64;                       // bit: the entry's voxel is in the hull
 constexpr int64_t kMaxRowEntries = 1 << 16;      // longer stored rows are reported, not read
 
 __device__ __forceinline__ RunSlots row_slots(unsigned char* smem)
@@ -217,7 +220,7 @@ struct PackWriter {
             if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1)
                 atomicOr(flags, kFlagPackStep);   // not a neighbouring voxel: cannot be coded
             else
-                code = (uint8_t)((dx + 1) + 3 * (dy + 1) + 9 * (dz + 1));
+                code = (uint8_t)((dx + 1) | ((dy + 1) << 2) | ((dz + 1) << 4));
         }
         if (g.inside(qx, qy, qz) && __ldg(mask + g.index(qx, qy, qz))) code |= kCodeInside;
         uint16_t u;
@@ -447,9 +450,8 @@ __device__ __forceinline__ void unpack32(const uint8_t* __restrict__ codes,
     const int code = valid ? (int)__ldg(codes + e) : (int)kCodeStart;
     const uint16_t raw = valid ? lens[e] : (uint16_t)0;
     l = unit > 0.f ? (float)raw * unit : __half2float(__ushort_as_half(raw));
-    const int st = code & 31;
-    const int dx = st % 3, dy = (st / 3) % 3, dz = st / 9;   // each 0..2 (step + 1)
-    int p = dx | (dy << 10) | (dz << 20);
+    // the three steps + 1 (each 0..2) into 10-bit fields, summed by one scan
+    int p = (code & 3) | ((code & 12) << 8) | ((code & 48) << 16);
 #pragma unroll
     for (int o = 1; o < kWarp; o <<= 1) {
         const int u = __shfl_up_sync(0xffffffffu, p, o);
