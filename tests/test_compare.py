@@ -126,3 +126,30 @@ def test_residual_part_excludes_the_voxels_of_a_row_whose_residual_moved():
     exr.add(0, gi, gl, nnz, rowptr, j, ln, margin, cond)
     exr.finish()
     assert exr.rows_resid == 0 and np.nonzero(exr.mask)[0].tolist() == [4, 5]
+
+
+def test_residual_part_is_relative_to_the_voxel_value():
+    # a small residual change: below RESID_TOL x_j where x_j = 1, above it on a
+    # voxel whose value is 0.01 (the RSP tolerance is relative)
+    rowptr, j, ln = _rows()
+    gi, gl, nnz = _pad(rowptr, j, ln)
+    gl[2, 2] += 1e-4                     # row 2: voxels 3, 6, 7; the last chord 1e-4 mm longer
+    margin, cond = np.zeros(3), np.ones(3)
+    b = np.array([2.2, 1.5, 3.0])
+    x = np.ones(10)
+    r_o = (3.0 - 2.2) / (0.81 + 1.21 + 0.04)
+    r_g = (3.0 - 2.2 - 1e-4) / (0.81 + 1.21 + (0.2 + 1e-4) ** 2)
+    dr = abs(r_g - r_o)
+    assert 1.1 * dr < RESID_TOL * 1.0      # the longest chord on a voxel of value 1: kept
+    assert 0.9 * dr > RESID_TOL * 0.01     # the 0.9 mm chord on a voxel of value 0.01: left out
+    ex = Exclusion(10, 3, x=x, b=b)
+    ex.add(0, gi, gl, nnz, rowptr, j, ln, margin, cond)
+    ex.finish()
+    assert not ex.resid.any()
+    x[3] = 0.01
+    b2 = b.copy()
+    b2[2] = 3.0 - 0.9 + 0.009            # keep the residual the same size with x_3 = 0.01
+    ex = Exclusion(10, 3, x=x, b=b2)
+    ex.add(0, gi, gl, nnz, rowptr, j, ln, margin, cond)
+    ex.finish()
+    assert np.nonzero(ex.resid)[0].tolist() == [3]
