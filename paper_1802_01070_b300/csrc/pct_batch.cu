@@ -74,8 +74,7 @@ k_drop_batch(const ScanDesc* __restrict__ scans, int nscan, unsigned* flags, int
     const int nwarp = d.ncta * warps;
     const int tid_in_scan = ((int)blockIdx.x - d.cta0) * blockDim.x + threadIdx.x;
     const int nthr = d.ncta * blockDim.x;
-    unsigned char* base = smem + (size_t)(threadIdx.x >> 5) * kBatchRunSlots * kWarp * 8;
-    const RunSlots slots{(int*)base, (float*)(base + (size_t)kBatchRunSlots * kWarp * 4)};
+    const RunSlots slots{(int2*)(smem + (size_t)(threadIdx.x >> 5) * kBatchRunSlots * kWarp * 8)};
     const RecView rv{d.rec, d.stride};
     // only the first barrier of scan 0 is made unreachable by the test option
     int extra = (test_unreachable && s == 0) ? 1 : 0;

@@ -232,8 +232,15 @@ constexpr int kRowSlots = 64;
 __device__ __forceinline__ RunSlots warp_slots(unsigned char* smem, int rl)
 {
     const int warp = threadIdx.x >> 5;
+    return RunSlots{(int2*)(smem + (size_t)warp * rl * kWarp * 8)};
+}
+
+// The same bytes as the round walk's run list (voxel array, then chord array).
+__device__ __forceinline__ RunList warp_list(unsigned char* smem, int rl)
+{
+    const int warp = threadIdx.x >> 5;
     unsigned char* base = smem + (size_t)warp * rl * kWarp * 8;
-    return RunSlots{(int*)base, (float*)(base + (size_t)rl * kWarp * 4)};
+    return RunList{(int*)base, (float*)(base + (size_t)rl * kWarp * 4)};
 }
 
 // Rows of A in path order (debug / parity), one warp per proton.
@@ -405,7 +412,7 @@ k_drop_rounds(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, un
 {
     extern __shared__ unsigned char smem[];
     const RunSlots slots = warp_slots(smem, kRunSlots);
-    const RunList list{slots.j, slots.l};
+    const RunList list = warp_list(smem, kRunSlots);
     const int lane = threadIdx.x & (kWarp - 1);
     const int64_t lo = boff[k];
     for_each_item(boff[k + 1] - lo, first, next, [&](int64_t t) {
@@ -467,7 +474,7 @@ k_rows_rounds(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, un
         return;
     }
     const RunSlots slots = warp_slots(smem, kRowSlots);
-    const RunList list{slots.j, slots.l};
+    const RunList list = warp_list(smem, kRowSlots);
     int32_t* oi = idx + t * (int64_t)max_nnz;
     float* ol = len + t * (int64_t)max_nnz;
     int total = 0;

@@ -30,8 +30,7 @@ constexpr int64_t kMaxRowEntries = 1 << 16;      // longer stored rows are repor
 __device__ __forceinline__ RunSlots row_slots(unsigned char* smem)
 {
     const int warp = threadIdx.x >> 5;
-    unsigned char* base = smem + (size_t)warp * kRunSlotsRows * kWarp * 8;
-    return RunSlots{(int*)base, (float*)(base + (size_t)kRunSlotsRows * kWarp * 4)};
+    return RunSlots{(int2*)(smem + (size_t)warp * kRunSlotsRows * kWarp * 8)};
 }
 
 __device__ __forceinline__ int warp_sum_int(int v)
@@ -71,7 +70,7 @@ k_csr_count(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsi
     }
     LaneWalk w;
     float s, q;
-    warp_walk<0, false>(P, mc, g, mask, nullptr, flags, RunSlots{nullptr, nullptr}, mc.cmin, w, s, q);
+    warp_walk<0, false>(P, mc, g, mask, nullptr, flags, RunSlots{nullptr}, mc.cmin, w, s, q);
     const int mine = (w.k0 < w.k1) ? w.n - ((w.merged_prev && w.head_in) ? 1 : 0) : 0;
     const int total = warp_sum_int(mine);
     if ((threadIdx.x & 31) == 0) cnt[i] = total;

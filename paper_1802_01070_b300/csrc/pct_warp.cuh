@@ -23,10 +23,14 @@ namespace pct {
 
 constexpr int kWarp = 32;
 
-// Per-warp shared-memory slots of stored runs: j[e * 32 + lane], l[e * 32 + lane].
+// Per-warp shared-memory slots of stored runs: r[e * 32 + lane] = (voxel,
+// chord bits), one 8-byte store and load per run.
 struct RunSlots {
-    int* j;
-    float* l;
+    int2* r;
+    __device__ __forceinline__ void put(int e, int lane, int j, float l) const
+    {
+        r[e * 32 + lane] = make_int2(j, __float_as_int(l));
+    }
 };
 
 
@@ -102,14 +106,15 @@ __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const
         const float ex = Dx * g.dx, ey = Dy * g.dy, ez = Dz * g.dz;
         const float l2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
         const float len = l2 > 0.f ? l2 * rsqrtf(l2) : 0.f;
-        const int sx = Dx > 0.f ? 1 : -1, sy = Dy > 0.f ? 1 : -1, sz = Dz > 0.f ? 1 : -1;
+        const bool px = Dx > 0.f, py = Dy > 0.f, pz = Dz > 0.f;
+        const int sx = px ? 1 : -1, sy = py ? 1 : -1, sz = pz ? 1 : -1;
         const float rx = __fdividef(1.f, Dx), ry = __fdividef(1.f, Dy), rz = __fdividef(1.f, Dz);
-        float tmx = Dx > 0.f ? (float)(ix + 1) - ax : (Dx < 0.f ? (float)ix - ax : INF);
-        float tmy = Dy > 0.f ? (float)(iy + 1) - ay : (Dy < 0.f ? (float)iy - ay : INF);
-        float tmz = Dz > 0.f ? (float)(iz + 1) - az : (Dz < 0.f ? (float)iz - az : INF);
-        if (Dx != 0.f) tmx *= rx;
-        if (Dy != 0.f) tmy *= ry;
-        if (Dz != 0.f) tmz *= rz;
+        // parameter of the first face crossed on each axis ((float)ix + 1 is
+        // exact: grids hold fewer than 2^24 voxels along an axis); none on an
+        // axis the segment does not move along
+        float tmx = Dx != 0.f ? ((float)ix + (px ? 1.f : 0.f) - ax) * rx : INF;
+        float tmy = Dy != 0.f ? ((float)iy + (py ? 1.f : 0.f) - ay) * ry : INF;
+        float tmz = Dz != 0.f ? ((float)iz + (pz ? 1.f : 0.f) - az) * rz : INF;
         const float tdx = fabsf(rx), tdy = fabsf(ry), tdz = fabsf(rz);
         const int guard = (int)(fabsf(Dx) + fabsf(Dy) + fabsf(Dz)) + 4;
         float t = 0.f;
@@ -169,25 +174,13 @@ struct StoreSink {
     uint8_t pm;
     bool pending;
 
+    // the pending run (there is one) is final: count, accumulate and store it
     __device__ __forceinline__ void commit()
     {
-        if (!pending) return;
-        if (!w->any) {
-            w->any = true;
-            w->head_j = pj;
-            w->head_l = pl;
-            w->head_in = pm != 0;
-        }
-        w->tail_j = pj;
-        w->tail_l = pl;
-        w->tail_in = pm != 0;
         if (pm) {
             if (DOT) w->s = fmaf(pl, px, w->s);
             w->q = fmaf(pl, pl, w->q);
-            if (w->n < RL) {
-                slots.j[w->n * kWarp + lane] = pj;
-                slots.l[w->n * kWarp + lane] = pl;
-            }
+            if (w->n < RL) slots.put(w->n, lane, pj, pl);
             ++w->n;
         }
     }
@@ -201,7 +194,12 @@ struct StoreSink {
             m = __ldg(mask + j);
             if (DOT) xv = CG ? __ldcg(x + j) : __ldg(x + j);
         }
-        commit();
+        if (pending) {
+            commit();
+        } else {   // the lane's first raw run
+            w->head_j = j;
+            w->head_l = l;
+        }
         pj = j;
         pl = l;
         px = xv;
@@ -245,7 +243,21 @@ __device__ __forceinline__ void warp_walk(const Path& P, const MlpC& mc, const G
     if (w.k0 < w.k1) {
         StoreSink<RL, DOT, CG> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, wl, &w, -1, 0.f, 0.f, 0, false};
         walk_points(P, mc, g, flags, w.k0, w.k1, w.ends, sink);
-        sink.commit();
+        if (sink.pending) {
+            sink.commit();
+            // the pending run after the walk is the lane's last raw run
+            w.any = true;
+            w.tail_j = sink.pj;
+            w.tail_l = sink.pl;
+            w.tail_in = sink.pm != 0;
+            // the first raw run is a hull run exactly when it is the first
+            // stored run: a voxel outside the hull is never stored, and a
+            // later hull run lies in another voxel
+            if (RL > 0)
+                w.head_in = w.n > 0 && w.head_j >= 0 && slots.r[wl].x == w.head_j;
+            else
+                w.head_in = w.head_j >= 0 && __ldg(mask + w.head_j) != 0;
+        }
     }
     const unsigned full = 0xffffffffu;
     const int pt_j = __shfl_up_sync(full, w.tail_j, 1, G);
@@ -316,11 +328,16 @@ __device__ __forceinline__ void replay_runs(const Path& P, const MlpC& mc, const
     if (w.k0 >= w.k1) return;
     const int lane = threadIdx.x & (kWarp - 1);
     if (w.n <= RL) {
-        for (int e = 0; e < w.n; ++e) {
-            if (e == 0 && w.merged_prev && w.head_in) continue;
-            float l = slots.l[e * kWarp + lane];
-            if (e == w.n - 1 && w.next_merges && w.tail_in) l += w.next_head_l;
-            op(slots.j[e * kWarp + lane], l);
+        // the head run goes to the previous lane when it continues that
+        // lane's tail; the tail run takes the next lane's head piece
+        const int e0 = (w.merged_prev && w.head_in) ? 1 : 0;
+        const int last = w.n - 1;
+        const float ext = (w.next_merges && w.tail_in) ? w.next_head_l : 0.f;
+        for (int e = e0; e < w.n; ++e) {
+            const int2 v = slots.r[e * kWarp + lane];
+            float l = __int_as_float(v.y);
+            if (e == last) l += ext;
+            op(v.x, l);
         }
     } else {
         RewalkSink<Op> sink{Dims{g.nx, g.ny, g.nz}, mask, &w, op, -1, 0.f, 0, false, true};

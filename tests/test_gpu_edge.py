@@ -228,3 +228,58 @@ def test_anisotropic_voxels_offset_origin_and_fine_mlp_step(cuda_device):
         assert not bad, bad[:5]
         assert excused <= 0.02 * rows
         ctx.close()
+
+
+def test_lanes_with_more_runs_than_slots(cuda_device):
+    """A lane whose range holds more runs than its 24 shared-memory slots walks
+    the runs beyond them again (once for the row's dot products, once for the
+    scatter).  0.25 mm voxels with a 5 mm MLP step put about 25 runs in every
+    lane's segment; one DROP block step from a known iterate must still match
+    the oracle's step under the comparison rule, and A x must match the
+    oracle's product."""
+    cfg0, rsp0, hull0, hist = U.scan("tiny")
+    h = _sub(hist, 0, 3000)
+    vox = 0.25
+    shape = (240, 240, 32)
+    origin = tuple(-0.5 * n * vox for n in shape)
+    nx, ny, nz = shape
+    z, y, x = np.meshgrid((np.arange(nz) + 0.5) * vox + origin[2],
+                          (np.arange(ny) + 0.5) * vox + origin[1],
+                          (np.arange(nx) + 0.5) * vox + origin[0], indexing="ij")
+    hull = ((x * x + y * y) <= 27.0 ** 2).astype(np.uint8).reshape(-1)
+    du_um = 5000
+    geo = O.Geometry(shape, (vox,) * 3, origin, mask=hull, du=du_um / 1000)
+    rowptr, j, ln, margin, cond = O.rows(geo, h, with_cond=True)
+    A = O.csr(rowptr, j, ln, geo.n_vox)
+    ctx = pct.Context(shape, (vox,) * 3, origin, hull=hull)
+    try:
+        ctx.set_option(pct.PCT_OPT_MLP_STEP_UM, du_um)
+        ctx.load_histories({k: torch.from_numpy(v).cuda() for k, v in h.items()})
+        # the workload reaches the overflow: with one segment per lane (the 5 mm
+        # step exceeds a voxel diagonal) a row whose runs outnumber 24 per
+        # segment has a lane beyond its slots
+        _, npts = ctx.mlp(0, len(h["wepl"]), max_pts=256)
+        nseg = np.maximum(npts.cpu().numpy() - 1, 1)
+        nnz = np.diff(rowptr)
+        assert int((nnz > 24 * nseg).sum()) >= 100
+        rng = np.random.default_rng(5)
+        x0 = (hull * (1.0 + 0.1 * rng.standard_normal(hull.size))).astype(np.float32)
+        xg = torch.from_numpy(x0).cuda()
+        yg = ctx.forward(xg).cpu().numpy().astype(np.float64)
+        yo = A @ x0.astype(np.float64)
+        ok = ~np.array([U.near_face(margin[i], cond[i]) for i in range(len(yo))])
+        assert np.max(np.abs(yg - yo)[ok] / np.maximum(np.abs(yo[ok]), 1.0)) <= 1e-4
+        n = len(h["wepl"])
+        b = h["wepl"].astype(np.float64)
+        ctx.solve(xg, 1, 0.5, n)
+        ctx.synchronize()
+        xs = xg.cpu().numpy().astype(np.float64)
+        xo = O.drop(A, b, 1, 0.5, n, x0.astype(np.float64))
+        ex = U.gpu_exclusion(ctx, rowptr, j, ln, margin, cond, n, x=x0.astype(np.float64), b=b)
+        r = U.solve_parity(xs, xo, hull, ex)
+        print(r)
+        assert r["rows_unexcused"] == 0, ex.unexcused[:10]
+        assert r["clean_max"] <= 1e-3
+        assert r["excluded"] <= 0.02 * hull.sum()
+    finally:
+        ctx.close()
