@@ -72,8 +72,27 @@ struct LaneWalk {
     float next_head_l;
 };
 
-// Walk the points k0..k1 of P (ends given); calls on_run(ix, iy, iz, chord) for
-// each maximal run of the path inside one voxel (positive chord), in path order.
+// Sinks of the walk come in two forms.  The run form has
+//   on_run(ix, iy, iz, chord)  for each maximal run of the path inside one
+//                              voxel (positive chord), in path order.
+// The voxel-entry form (kVoxelEntry = true) has
+//   start(ix, iy, iz)          the voxel the range starts in,
+//   enter(ix, iy, iz)          each voxel the walk steps into,
+//   emit(chord)                a run in the voxel last started or entered ends,
+//   emit_last(chord)           the range's final run,
+//   zero_run()                 a run of zero length was met (nothing emitted),
+// so that a sink can fetch what it needs of a voxel as soon as the walk steps
+// into it, one crossing before the run there is emitted.
+template <class F, class = void>
+struct VoxelEntrySink {
+    static constexpr bool value = false;
+};
+template <class F>
+struct VoxelEntrySink<F, decltype((void)F::kVoxelEntry)> {
+    static constexpr bool value = F::kVoxelEntry;
+};
+
+// Walk the points k0..k1 of P (ends given), reporting to the sink on_run.
 template <class F>
 __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const GridC& g,
                                             unsigned* flags, int k0, int k1, const RangeEnds& re,
@@ -90,6 +109,8 @@ __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const
     int ix = start_index(ax, bx - ax);
     int iy = start_index(ay, by - ay);
     int iz = start_index(az, bz - az);
+    constexpr bool kEntry = VoxelEntrySink<F>::value;
+    if constexpr (kEntry) on_run.start(ix, iy, iz);
     float run = 0.f;
     const float INF = __int_as_float(0x7f800000);
     for (int k = k0 + 1; k <= k1; ++k) {
@@ -127,11 +148,19 @@ __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const
             }
             const float tc = fmaxf(tn, t);
             run = fmaf(tc - t, len, run);
-            if (run > 0.f) on_run(ix, iy, iz, run);
+            if constexpr (kEntry) {
+                if (run > 0.f)
+                    on_run.emit(run);
+                else
+                    on_run.zero_run();
+            } else {
+                if (run > 0.f) on_run(ix, iy, iz, run);
+            }
             run = 0.f;
             if (tmx == tn) { ix += sx; tmx += tdx; }
             if (tmy == tn) { iy += sy; tmy += tdy; }
             if (tmz == tn) { iz += sz; tmz += tdz; }
+            if constexpr (kEntry) on_run.enter(ix, iy, iz);
             t = tc;
             if (++nstep > guard) {
                 atomicOr(flags, kFlagWalkGuard);
@@ -142,12 +171,16 @@ __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const
         ay = by;
         az = bz;
     }
-    if (run > 0.f) on_run(ix, iy, iz, run);
+    if constexpr (kEntry) {
+        if (run > 0.f)
+            on_run.emit_last(run);
+        else
+            on_run.zero_run();
+    } else {
+        if (run > 0.f) on_run(ix, iy, iz, run);
+    }
 }
 
-// Pass-1 run sink: the hull byte (and x) of a run are loaded when the run is
-// emitted and used when the next run is emitted, so the loads overlap the
-// arithmetic of the walk.
 // Grid extent a sink needs (passed by value: taking the address of a kernel
 // parameter would force a stack copy).
 struct Dims {
@@ -159,8 +192,68 @@ struct Dims {
     __device__ __forceinline__ int index(int ix, int iy, int iz) const { return ix + nx * (iy + ny * iz); }
 };
 
+// Pass-1 sink in the voxel-entry form: the hull byte (and x) of a voxel are
+// loaded when the walk steps into it and used when the run there ends, one
+// crossing later, so the loads overlap the walk's arithmetic with no per-run
+// copies.  Hull runs are counted, accumulated into s = a_i.x and q =
+// ||a_i||^2 and stored (the first RL).  With no run of zero length, the lane's
+// first raw run lies in the voxel its range starts in and its last raw run in
+// the voxel the range ends in; a zero-length run sets `odd`, and the caller
+// then walks the lane again with StoreSink.
 // CG: read x through L2 only (ld.global.cg), for kernels in which other CTAs
 // rewrite x between barriers; otherwise the read-only cache path.
+template <int RL, bool DOT, bool CG = false>
+struct EntrySink {
+    static constexpr bool kVoxelEntry = true;
+    Dims g;
+    const uint8_t* __restrict__ mask;
+    const float* __restrict__ x;
+    RunSlots slots;
+    int lane;
+    int n;
+    float s, q;
+    int j, j0;     // voxel the walk is in, voxel the range starts in (-1 outside the grid)
+    float xv;      // x of voxel j (DOT)
+    float last;    // chord of the range's final run
+    uint8_t m;     // hull byte of voxel j
+    bool odd;
+
+    __device__ __forceinline__ void enter(int ix, int iy, int iz)
+    {
+        j = -1;
+        m = 0;
+        xv = 0.f;
+        if (g.inside(ix, iy, iz)) {
+            j = g.index(ix, iy, iz);
+            m = __ldg(mask + j);
+            if (DOT) xv = CG ? __ldcg(x + j) : __ldg(x + j);
+        }
+    }
+    __device__ __forceinline__ void start(int ix, int iy, int iz)
+    {
+        enter(ix, iy, iz);
+        j0 = j;
+    }
+    __device__ __forceinline__ void emit(float l)
+    {
+        if (m) {
+            if (DOT) s = fmaf(l, xv, s);
+            q = fmaf(l, l, q);
+            if (n < RL) slots.put(n, lane, j, l);
+            ++n;
+        }
+    }
+    __device__ __forceinline__ void emit_last(float l)
+    {
+        emit(l);
+        last = l;
+    }
+    __device__ __forceinline__ void zero_run() { odd = true; }
+};
+
+// Pass-1 sink in the run form (the exact fallback of EntrySink, and the walk
+// of kernels without run slots): the hull byte (and x) of a run are loaded
+// when the run is emitted and used when the next run is emitted.
 template <int RL, bool DOT, bool CG = false>
 struct StoreSink {
     Dims g;
@@ -240,7 +333,30 @@ __device__ __forceinline__ void warp_walk(const Path& P, const MlpC& mc, const G
     w.head_in = w.tail_in = false;
     w.s = w.q = 0.f;
     w.ends = range_ends<G>(P, mc, g, w.k0, w.k1);
-    if (w.k0 < w.k1) {
+    bool exact = RL == 0;
+    if (RL > 0 && w.k0 < w.k1) {
+        EntrySink<RL, DOT, CG> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, wl, 0, 0.f, 0.f, -1, -1, 0.f, 0.f, 0, false};
+        walk_points(P, mc, g, flags, w.k0, w.k1, w.ends, sink);
+        if (!sink.odd) {
+            w.n = sink.n;
+            w.s = sink.s;
+            w.q = sink.q;
+            w.any = true;
+            w.tail_j = sink.j;
+            w.tail_l = sink.last;
+            w.tail_in = sink.m != 0;
+            w.head_j = sink.j0;
+            // the first raw run is a hull run exactly when it is the first
+            // stored run (a voxel outside the hull is never stored, and a
+            // later hull run lies in another voxel); only then does its
+            // chord matter
+            w.head_in = w.n > 0 && w.head_j >= 0 && slots.r[wl].x == w.head_j;
+            if (w.head_in) w.head_l = __int_as_float(slots.r[wl].y);
+        } else {
+            exact = true;
+        }
+    }
+    if (exact && w.k0 < w.k1) {
         StoreSink<RL, DOT, CG> sink{Dims{g.nx, g.ny, g.nz}, mask, x, slots, wl, &w, -1, 0.f, 0.f, 0, false};
         walk_points(P, mc, g, flags, w.k0, w.k1, w.ends, sink);
         if (sink.pending) {
