@@ -35,7 +35,8 @@ void mlp_sigma_table(double du_mm, int kmax, float4* tab)
                 mom[n] += kCoef200[p] * std::pow(w, n + p + 1) * fact[n] * fact[p] / fact[n + p + 1];
         const double lf = 1.0 + 0.038 * std::log(w / (double)kX0);
         const double pre = (double)kE0 * (double)kE0 * lf * lf / (double)kX0;
-        tab[k] = make_float4((float)(pre * mom[2]), (float)(pre * mom[1]), (float)(pre * mom[0]), 0.f);
+        tab[k] = make_float4((float)(pre * mom[2]), (float)(pre * mom[1]), (float)(pre * mom[0]),
+                             (float)(2.0 * pre * mom[1]));
     }
 }
 

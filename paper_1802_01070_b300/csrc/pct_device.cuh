@@ -47,7 +47,7 @@ struct GridC {
 struct MlpC {
     float du_mm, du_cm, dend_mm;
     float coef[6];        // 1/(beta^2 p^2) = sum coef[k] u^k, MeV^-2, u in cm
-    const float4* sig1;   // sig1[k] = Sigma(0, k*du): (S00, S01, S11, 0), cm / rad
+    const float4* sig1;   // sig1[k] = Sigma(0, k*du): (S00, S01, S11, 2 S01), cm / rad
     int kmax;             // last valid index of sig1
     int cmin;             // fewest segments per lane range whose depth exceeds a voxel diagonal
 };
@@ -148,7 +148,7 @@ __device__ __forceinline__ void mlp_offset(const Path& P, const MlpC& mc, int k,
     const float T11 = pre * q0;             // Sigma2 entries (cm, rad)
     const float T01 = pre * W * q1;
     const float T00 = pre * W * W * q2;
-    const float M00 = fmaf(W, fmaf(W, s1.z, 2.f * s1.y), s1.x) + T00;
+    const float M00 = fmaf(W, fmaf(W, s1.z, s1.w), s1.x) + T00;
     const float M01 = fmaf(W, s1.z, s1.y) + T01;
     const float M11 = s1.z + T11;
     const float g0 = fmaf(W, s1.y, s1.x);

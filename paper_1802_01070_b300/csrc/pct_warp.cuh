@@ -142,8 +142,11 @@ __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const
         int nstep = 0;
         for (;;) {
             const float tn = fminf(tmx, fminf(tmy, tmz));
-            if (!(tn < 1.f)) {
-                run = fmaf(1.f - t, len, run);
+            if (!(tn < 1.f) || nstep > guard) {
+                if (nstep > guard)
+                    atomicOr(flags, kFlagWalkGuard);
+                else
+                    run = fmaf(1.f - t, len, run);
                 break;
             }
             const float tc = fmaxf(tn, t);
@@ -162,10 +165,7 @@ __device__ __forceinline__ void walk_points(const Path& P, const MlpC& mc, const
             if (tmz == tn) { iz += sz; tmz += tdz; }
             if constexpr (kEntry) on_run.enter(ix, iy, iz);
             t = tc;
-            if (++nstep > guard) {
-                atomicOr(flags, kFlagWalkGuard);
-                break;
-            }
+            ++nstep;
         }
         ax = bx;
         ay = by;
