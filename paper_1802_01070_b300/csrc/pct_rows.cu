@@ -26,6 +26,9 @@ constexpr int kScanChunk = kScanCta * kScanPer;  // elements per CTA
 constexpr uint8_t kCodeStart = 1 | (1 << 2) | (1 << 4);   // step (0, 0, 0): the row's first run
 constexpr uint8_t kCodeInside = 64;                       // bit: the entry's voxel is in the hull
 constexpr int64_t kMaxRowEntries = 1 << 16;      // longer stored rows are reported, not read
+// Packed rows start on groups of 4 entries (padded at their end), so that a
+// lane of the DROP step loads the codes and chords of 4 entries at once.
+constexpr int kPackAlign = 4;
 
 __device__ __forceinline__ RunSlots row_slots(unsigned char* smem)
 {
@@ -186,7 +189,7 @@ k_pack_count(GridC g, MlpC mc, RecView rv, unsigned* flags, int64_t m, int32_t* 
     const int mine = r.n - (pm.merged_prev ? 1 : 0);
     const int total = warp_sum_int(mine);
     if ((threadIdx.x & 31) == 0) {
-        cnt[i] = total;
+        cnt[i] = (total + kPackAlign - 1) & ~(kPackAlign - 1);   // padded to whole groups
         start[i] = make_short4((short)r.hx, (short)r.hy, (short)r.hz, 0);
     }
 }
@@ -275,6 +278,15 @@ k_pack_fill(GridC g, MlpC mc, RecView rv, const uint8_t* __restrict__ mask, unsi
     const int mine = r.n - (pm.merged_prev ? 1 : 0);
     int total;
     const int64_t off = rowptr[i] + warp_excl_scan(mine, total);
+    // padding entries up to the next whole group: no step, outside the hull,
+    // zero chord (the decoder skips them)
+    {
+        const int64_t pad = rowptr[i] + total + lane;
+        if (lane < kPackAlign - 1 && pad < rowptr[i + 1]) {
+            codes[pad] = kCodeStart;
+            lens[pad] = 0;
+        }
+    }
     if (k0 >= k1) return;
     // a lane other than the first codes its first run as a step from the previous
     // lane's last voxel; the row's first run is the "start" entry
@@ -436,40 +448,60 @@ k_drop_csr(unsigned* flags, const int64_t* __restrict__ rowptr, const int32_t* _
         atomicAdd(acc + __ldg(idx + e), make_float2(__ldg(len + e) * r, 1.f));
 }
 
-// Decode 32 packed entries starting at e0 into voxels (warp-cooperative): the
-// steps are prefix-summed across the lanes.
-__device__ __forceinline__ void unpack32(const uint8_t* __restrict__ codes,
-                                         const uint16_t* __restrict__ lens, float unit, int64_t e0, int64_t e1,
-                                         int& bx, int& by, int& bz, const Dims& g, int& j, float& l,
-                                         bool& inside)
+// Decode 128 entries of a packed row starting at e0 (a whole group): lane l
+// takes entries e0 + 4l .. e0 + 4l + 3 with one 4-byte load of their codes and
+// one 8-byte load of their chords, sums their steps in the lane, and one warp
+// scan of the lanes' sums places them.  (bx, by, bz) is the voxel before e0
+// and is advanced past the 128 entries.  Entries at or beyond e1 decode as
+// outside the hull.
+__device__ __forceinline__ void unpack128(const uint8_t* __restrict__ codes,
+                                          const uint16_t* __restrict__ lens, float unit, int64_t e0, int64_t e1,
+                                          int& bx, int& by, int& bz, const Dims& g, int (&j)[4], float (&l)[4],
+                                          bool (&inside)[4])
 {
     const int lane = threadIdx.x & 31;
-    const int64_t e = e0 + lane;
-    const bool valid = e < e1;
-    const int code = valid ? (int)__ldg(codes + e) : (int)kCodeStart;
-    const uint16_t raw = valid ? lens[e] : (uint16_t)0;
-    l = unit > 0.f ? (float)raw * unit : __half2float(__ushort_as_half(raw));
-    // the three steps + 1 (each 0..2) into 10-bit fields, summed by one scan
-    int p = (code & 3) | ((code & 12) << 8) | ((code & 48) << 16);
+    const int64_t e = e0 + 4 * lane;
+    const bool valid = e < e1;   // e1 is a whole group: all four entries or none
+    const uint32_t c4 = valid ? __ldg((const uint32_t*)(codes + e)) : 0x01010101u * kCodeStart;
+    const uint2 r4 = valid ? __ldg((const uint2*)(lens + e)) : make_uint2(0u, 0u);
+    int code[4], p[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        code[u] = (int)((c4 >> (8 * u)) & 0xffu);
+        // the three steps + 1 (each 0..2) into 10-bit fields
+        p[u] = (code[u] & 3) | ((code[u] & 12) << 8) | ((code[u] & 48) << 16);
+    }
+    p[1] += p[0];
+    p[2] += p[1];
+    p[3] += p[2];
+    int sc = p[3];
 #pragma unroll
     for (int o = 1; o < kWarp; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, p, o);
-        if (lane >= o) p += u;
+        const int v = __shfl_up_sync(0xffffffffu, sc, o);
+        if (lane >= o) sc += v;
     }
-    const int c = lane + 1;
-    const int ix = bx + (p & 1023) - c, iy = by + ((p >> 10) & 1023) - c, iz = bz + ((p >> 20) & 1023) - c;
-    const int pt = __shfl_sync(0xffffffffu, p, 31);
-    bx += (pt & 1023) - 32;
-    by += ((pt >> 10) & 1023) - 32;
-    bz += ((pt >> 20) & 1023) - 32;
-    inside = valid && (code & kCodeInside);
-    j = inside ? g.index(ix, iy, iz) : 0;
+    const int excl = sc - p[3];
+    const int pt = __shfl_sync(0xffffffffu, sc, 31);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int q = excl + p[u];
+        const int c = 4 * lane + u + 1;
+        const int ix = bx + (q & 1023) - c, iy = by + ((q >> 10) & 1023) - c, iz = bz + ((q >> 20) & 1023) - c;
+        inside[u] = valid && (code[u] & kCodeInside);
+        j[u] = inside[u] ? g.index(ix, iy, iz) : 0;
+        const uint32_t w = u < 2 ? r4.x : r4.y;
+        const uint16_t raw = (uint16_t)((u & 1) ? (w >> 16) : (w & 0xffffu));
+        l[u] = unit > 0.f ? (float)raw * unit : __half2float(__ushort_as_half(raw));
+    }
+    bx += (pt & 1023) - 128;
+    by += ((pt >> 10) & 1023) - 128;
+    bz += ((pt >> 20) & 1023) - 128;
 }
 
-// Chunks of 32 entries of a packed row that the DROP step decodes once and
+// Groups of 128 entries of a packed row that the DROP step decodes once and
 // keeps in registers for the scatter (a torso row has ~224 entries); the
 // entries beyond them are decoded again for the scatter.
-constexpr int kPackedKeep = 8;
+constexpr int kPackedKeep = 2;
 
 __global__ void __launch_bounds__(kRowCta)
 k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, const short4* __restrict__ start,
@@ -482,61 +514,74 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
     const int64_t i = first + t;
     const int64_t a = rowptr[i], e1 = rowptr[i + 1];
     if (a == e1) return;
-    if (e1 < a || e1 - a > kMaxRowEntries) {
+    if (e1 < a || e1 - a > kMaxRowEntries || ((a | e1) & (kPackAlign - 1))) {
         if ((threadIdx.x & 31) == 0) atomicOr(flags, kFlagRowBounds);
         return;
     }
     const Dims g{gc.nx, gc.ny, gc.nz};
     const int nvox = gc.nx * gc.ny * gc.nz;
     const short4 s0 = start[i];
-    const int64_t nchunk = (e1 - a + kWarp - 1) / kWarp;
+    const int64_t ngroup = (e1 - a + 4 * kWarp - 1) / (4 * kWarp);
     int bx = s0.x, by = s0.y, bz = s0.z;
-    // the kept chunks: decode all, then gather x, then accumulate in entry order
-    int jk[kPackedKeep];
-    float lk[kPackedKeep], xk[kPackedKeep];
+    // the kept groups: decode all, then gather x, then accumulate in entry order
+    int jk[kPackedKeep][4];
+    float lk[kPackedKeep][4], xk[kPackedKeep][4];
 #pragma unroll
     for (int c = 0; c < kPackedKeep; ++c) {
-        jk[c] = -1;
-        lk[c] = 0.f;
-        if (c < nchunk) {   // warp-uniform
-            int j;
-            float l;
-            bool in;
-            unpack32(codes, lens, unit, a + c * kWarp, e1, bx, by, bz, g, j, l, in);
-            if (in && (unsigned)j >= (unsigned)nvox) {
-                atomicOr(flags, kFlagRowBounds);
-                in = false;
-            }
-            if (in) {
-                jk[c] = j;
-                lk[c] = l;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            jk[c][u] = -1;
+            lk[c][u] = 0.f;
+        }
+        if (c < ngroup) {   // warp-uniform
+            int j[4];
+            float l[4];
+            bool in[4];
+            unpack128(codes, lens, unit, a + c * 4 * kWarp, e1, bx, by, bz, g, j, l, in);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (in[u] && (unsigned)j[u] >= (unsigned)nvox) {
+                    atomicOr(flags, kFlagRowBounds);
+                    in[u] = false;
+                }
+                if (in[u]) {
+                    jk[c][u] = j[u];
+                    lk[c][u] = l[u];
+                }
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < kPackedKeep; ++c) xk[c] = jk[c] >= 0 ? __ldg(x + jk[c]) : 0.f;
+    for (int c = 0; c < kPackedKeep; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xk[c][u] = jk[c][u] >= 0 ? __ldg(x + jk[c][u]) : 0.f;
     float s = 0.f, q = 0.f;
 #pragma unroll
-    for (int c = 0; c < kPackedKeep; ++c) {
-        if (jk[c] >= 0) {
-            s = fmaf(lk[c], xk[c], s);
-            q = fmaf(lk[c], lk[c], q);
+    for (int c = 0; c < kPackedKeep; ++c)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (jk[c][u] >= 0) {
+                s = fmaf(lk[c][u], xk[c][u], s);
+                q = fmaf(lk[c][u], lk[c][u], q);
+            }
         }
-    }
     // the rest of a long row
     const int kx = bx, ky = by, kz = bz;
-    for (int64_t e0 = a + kPackedKeep * kWarp; e0 < e1; e0 += kWarp) {
-        int j;
-        float l;
-        bool in;
-        unpack32(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
-        if (in && (unsigned)j >= (unsigned)nvox) {
-            atomicOr(flags, kFlagRowBounds);
-            in = false;
-        }
-        if (in) {
-            s = fmaf(l, __ldg(x + j), s);
-            q = fmaf(l, l, q);
+    for (int64_t e0 = a + kPackedKeep * 4 * kWarp; e0 < e1; e0 += 4 * kWarp) {
+        int j[4];
+        float l[4];
+        bool in[4];
+        unpack128(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (in[u] && (unsigned)j[u] >= (unsigned)nvox) {
+                atomicOr(flags, kFlagRowBounds);
+                in[u] = false;
+            }
+            if (in[u]) {
+                s = fmaf(l[u], __ldg(x + j[u]), s);
+                q = fmaf(l[u], l[u], q);
+            }
         }
     }
 #pragma unroll
@@ -548,16 +593,20 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
     const float r = (__ldg(b + i) - s) / q;
 #pragma unroll
     for (int c = 0; c < kPackedKeep; ++c)
-        if (jk[c] >= 0) atomicAdd(acc + jk[c], make_float2(lk[c] * r, 1.f));
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (jk[c][u] >= 0) atomicAdd(acc + jk[c][u], make_float2(lk[c][u] * r, 1.f));
     bx = kx;
     by = ky;
     bz = kz;
-    for (int64_t e0 = a + kPackedKeep * kWarp; e0 < e1; e0 += kWarp) {
-        int j;
-        float l;
-        bool in;
-        unpack32(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
-        if (in && (unsigned)j < (unsigned)nvox) atomicAdd(acc + j, make_float2(l * r, 1.f));
+    for (int64_t e0 = a + kPackedKeep * 4 * kWarp; e0 < e1; e0 += 4 * kWarp) {
+        int j[4];
+        float l[4];
+        bool in[4];
+        unpack128(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (in[u] && (unsigned)j[u] < (unsigned)nvox) atomicAdd(acc + j[u], make_float2(l[u] * r, 1.f));
     }
 }
 
