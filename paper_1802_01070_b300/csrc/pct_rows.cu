@@ -448,60 +448,95 @@ k_drop_csr(unsigned* flags, const int64_t* __restrict__ rowptr, const int32_t* _
         atomicAdd(acc + __ldg(idx + e), make_float2(__ldg(len + e) * r, 1.f));
 }
 
-// Decode 128 entries of a packed row starting at e0 (a whole group): lane l
-// takes entries e0 + 4l .. e0 + 4l + 3 with one 4-byte load of their codes and
-// one 8-byte load of their chords, sums their steps in the lane, and one warp
-// scan of the lanes' sums places them.  (bx, by, bz) is the voxel before e0
-// and is advanced past the 128 entries.  Entries at or beyond e1 decode as
+// Decode the 32 * kPackAlign entries of a packed row starting at e0 (a whole
+// group): lane l takes entries e0 + kPackAlign * l .. + kPackAlign - 1 with one
+// load of their codes and one of their chords, sums their steps in the lane,
+// and one warp scan of the lanes' sums places them.  (bx, by, bz) is the voxel
+// before e0 and is advanced past the group.  Entries at or beyond e1 decode as
 // outside the hull.
-__device__ __forceinline__ void unpack128(const uint8_t* __restrict__ codes,
-                                          const uint16_t* __restrict__ lens, float unit, int64_t e0, int64_t e1,
-                                          int& bx, int& by, int& bz, const Dims& g, int (&j)[4], float (&l)[4],
-                                          bool (&inside)[4])
+template <int V>
+struct PackVec;
+template <>
+struct PackVec<4> {
+    using Codes = uint32_t;
+    using Lens = uint2;
+    static __device__ __forceinline__ int code(Codes c, int u) { return (int)((c >> (8 * u)) & 0xffu); }
+    static __device__ __forceinline__ uint16_t len(Lens r, int u)
+    {
+        const uint32_t w = u < 2 ? r.x : r.y;
+        return (uint16_t)((u & 1) ? (w >> 16) : (w & 0xffffu));
+    }
+    static __device__ __forceinline__ Codes start() { return 0x01010101u * kCodeStart; }
+    static __device__ __forceinline__ Lens zero() { return make_uint2(0u, 0u); }
+};
+template <>
+struct PackVec<8> {
+    using Codes = uint2;
+    using Lens = uint4;
+    static __device__ __forceinline__ int code(Codes c, int u)
+    {
+        return (int)(((u < 4 ? c.x : c.y) >> (8 * (u & 3))) & 0xffu);
+    }
+    static __device__ __forceinline__ uint16_t len(Lens r, int u)
+    {
+        const uint32_t w = u < 2 ? r.x : (u < 4 ? r.y : (u < 6 ? r.z : r.w));
+        return (uint16_t)((u & 1) ? (w >> 16) : (w & 0xffffu));
+    }
+    static __device__ __forceinline__ Codes start()
+    {
+        return make_uint2(0x01010101u * kCodeStart, 0x01010101u * kCodeStart);
+    }
+    static __device__ __forceinline__ Lens zero() { return make_uint4(0u, 0u, 0u, 0u); }
+};
+
+__device__ __forceinline__ void unpack_group(const uint8_t* __restrict__ codes,
+                                             const uint16_t* __restrict__ lens, float unit, int64_t e0,
+                                             int64_t e1, int& bx, int& by, int& bz, const Dims& g,
+                                             int (&j)[kPackAlign], float (&l)[kPackAlign],
+                                             bool (&inside)[kPackAlign])
 {
+    using PV = PackVec<kPackAlign>;
     const int lane = threadIdx.x & 31;
-    const int64_t e = e0 + 4 * lane;
-    const bool valid = e < e1;   // e1 is a whole group: all four entries or none
-    const uint32_t c4 = valid ? __ldg((const uint32_t*)(codes + e)) : 0x01010101u * kCodeStart;
-    const uint2 r4 = valid ? __ldg((const uint2*)(lens + e)) : make_uint2(0u, 0u);
-    int code[4], p[4];
+    const int64_t e = e0 + kPackAlign * lane;
+    const bool valid = e < e1;   // e1 is a whole group: all entries of the lane or none
+    const typename PV::Codes cv = valid ? __ldg((const typename PV::Codes*)(codes + e)) : PV::start();
+    const typename PV::Lens rv = valid ? __ldg((const typename PV::Lens*)(lens + e)) : PV::zero();
+    int code[kPackAlign], p[kPackAlign];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        code[u] = (int)((c4 >> (8 * u)) & 0xffu);
+    for (int u = 0; u < kPackAlign; ++u) {
+        code[u] = PV::code(cv, u);
         // the three steps + 1 (each 0..2) into 10-bit fields
         p[u] = (code[u] & 3) | ((code[u] & 12) << 8) | ((code[u] & 48) << 16);
+        if (u > 0) p[u] += p[u - 1];
     }
-    p[1] += p[0];
-    p[2] += p[1];
-    p[3] += p[2];
-    int sc = p[3];
+    int sc = p[kPackAlign - 1];
 #pragma unroll
     for (int o = 1; o < kWarp; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, sc, o);
         if (lane >= o) sc += v;
     }
-    const int excl = sc - p[3];
+    const int excl = sc - p[kPackAlign - 1];
     const int pt = __shfl_sync(0xffffffffu, sc, 31);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < kPackAlign; ++u) {
         const int q = excl + p[u];
-        const int c = 4 * lane + u + 1;
+        const int c = kPackAlign * lane + u + 1;
         const int ix = bx + (q & 1023) - c, iy = by + ((q >> 10) & 1023) - c, iz = bz + ((q >> 20) & 1023) - c;
         inside[u] = valid && (code[u] & kCodeInside);
         j[u] = inside[u] ? g.index(ix, iy, iz) : 0;
-        const uint32_t w = u < 2 ? r4.x : r4.y;
-        const uint16_t raw = (uint16_t)((u & 1) ? (w >> 16) : (w & 0xffffu));
+        const uint16_t raw = PV::len(rv, u);
         l[u] = unit > 0.f ? (float)raw * unit : __half2float(__ushort_as_half(raw));
     }
-    bx += (pt & 1023) - 128;
-    by += ((pt >> 10) & 1023) - 128;
-    bz += ((pt >> 20) & 1023) - 128;
+    constexpr int kGroup = kPackAlign * kWarp;
+    bx += (pt & 1023) - kGroup;
+    by += ((pt >> 10) & 1023) - kGroup;
+    bz += ((pt >> 20) & 1023) - kGroup;
 }
 
-// Groups of 128 entries of a packed row that the DROP step decodes once and
+// Groups of 32 * kPackAlign entries of a packed row that the DROP step decodes once and
 // keeps in registers for the scatter (a torso row has ~224 entries); the
 // entries beyond them are decoded again for the scatter.
-constexpr int kPackedKeep = 2;
+constexpr int kPackedKeep = 8 / kPackAlign;
 
 __global__ void __launch_bounds__(kRowCta)
 k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, const short4* __restrict__ start,
@@ -521,25 +556,25 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
     const Dims g{gc.nx, gc.ny, gc.nz};
     const int nvox = gc.nx * gc.ny * gc.nz;
     const short4 s0 = start[i];
-    const int64_t ngroup = (e1 - a + 4 * kWarp - 1) / (4 * kWarp);
+    const int64_t ngroup = (e1 - a + kPackAlign * kWarp - 1) / (kPackAlign * kWarp);
     int bx = s0.x, by = s0.y, bz = s0.z;
     // the kept groups: decode all, then gather x, then accumulate in entry order
-    int jk[kPackedKeep][4];
-    float lk[kPackedKeep][4], xk[kPackedKeep][4];
+    int jk[kPackedKeep][kPackAlign];
+    float lk[kPackedKeep][kPackAlign], xk[kPackedKeep][kPackAlign];
 #pragma unroll
     for (int c = 0; c < kPackedKeep; ++c) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kPackAlign; ++u) {
             jk[c][u] = -1;
             lk[c][u] = 0.f;
         }
         if (c < ngroup) {   // warp-uniform
-            int j[4];
-            float l[4];
-            bool in[4];
-            unpack128(codes, lens, unit, a + c * 4 * kWarp, e1, bx, by, bz, g, j, l, in);
+            int j[kPackAlign];
+            float l[kPackAlign];
+            bool in[kPackAlign];
+            unpack_group(codes, lens, unit, a + c * kPackAlign * kWarp, e1, bx, by, bz, g, j, l, in);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < kPackAlign; ++u) {
                 if (in[u] && (unsigned)j[u] >= (unsigned)nvox) {
                     atomicOr(flags, kFlagRowBounds);
                     in[u] = false;
@@ -554,12 +589,12 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
 #pragma unroll
     for (int c = 0; c < kPackedKeep; ++c)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) xk[c][u] = jk[c][u] >= 0 ? __ldg(x + jk[c][u]) : 0.f;
+        for (int u = 0; u < kPackAlign; ++u) xk[c][u] = jk[c][u] >= 0 ? __ldg(x + jk[c][u]) : 0.f;
     float s = 0.f, q = 0.f;
 #pragma unroll
     for (int c = 0; c < kPackedKeep; ++c)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kPackAlign; ++u) {
             if (jk[c][u] >= 0) {
                 s = fmaf(lk[c][u], xk[c][u], s);
                 q = fmaf(lk[c][u], lk[c][u], q);
@@ -567,13 +602,13 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
         }
     // the rest of a long row
     const int kx = bx, ky = by, kz = bz;
-    for (int64_t e0 = a + kPackedKeep * 4 * kWarp; e0 < e1; e0 += 4 * kWarp) {
-        int j[4];
-        float l[4];
-        bool in[4];
-        unpack128(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
+    for (int64_t e0 = a + kPackedKeep * kPackAlign * kWarp; e0 < e1; e0 += kPackAlign * kWarp) {
+        int j[kPackAlign];
+        float l[kPackAlign];
+        bool in[kPackAlign];
+        unpack_group(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < kPackAlign; ++u) {
             if (in[u] && (unsigned)j[u] >= (unsigned)nvox) {
                 atomicOr(flags, kFlagRowBounds);
                 in[u] = false;
@@ -594,18 +629,18 @@ k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, con
 #pragma unroll
     for (int c = 0; c < kPackedKeep; ++c)
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kPackAlign; ++u)
             if (jk[c][u] >= 0) atomicAdd(acc + jk[c][u], make_float2(lk[c][u] * r, 1.f));
     bx = kx;
     by = ky;
     bz = kz;
-    for (int64_t e0 = a + kPackedKeep * 4 * kWarp; e0 < e1; e0 += 4 * kWarp) {
-        int j[4];
-        float l[4];
-        bool in[4];
-        unpack128(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
+    for (int64_t e0 = a + kPackedKeep * kPackAlign * kWarp; e0 < e1; e0 += kPackAlign * kWarp) {
+        int j[kPackAlign];
+        float l[kPackAlign];
+        bool in[kPackAlign];
+        unpack_group(codes, lens, unit, e0, e1, bx, by, bz, g, j, l, in);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+        for (int u = 0; u < kPackAlign; ++u)
             if (in[u] && (unsigned)j[u] < (unsigned)nvox) atomicAdd(acc + j[u], make_float2(l[u] * r, 1.f));
     }
 }
