@@ -538,7 +538,9 @@ __device__ __forceinline__ void unpack_group(const uint8_t* __restrict__ codes,
 // entries beyond them are decoded again for the scatter.
 constexpr int kPackedKeep = 8 / kPackAlign;
 
-__global__ void __launch_bounds__(kRowCta)
+// 5 CTAs of 256 per SM (48 registers, a small spill): the step waits on its x
+// gathers, and 40 resident warps measured 4 % faster than 32 at 62 registers
+__global__ void __launch_bounds__(kRowCta, 5)
 k_drop_packed(GridC gc, unsigned* flags, const int64_t* __restrict__ rowptr, const short4* __restrict__ start,
               const uint8_t* __restrict__ codes, const uint16_t* __restrict__ lens, float unit,
               const float* __restrict__ b, int64_t first, int64_t count,
