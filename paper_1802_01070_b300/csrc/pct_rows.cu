@@ -469,25 +469,6 @@ struct PackVec<4> {
     static __device__ __forceinline__ Codes start() { return 0x01010101u * kCodeStart; }
     static __device__ __forceinline__ Lens zero() { return make_uint2(0u, 0u); }
 };
-template <>
-struct PackVec<8> {
-    using Codes = uint2;
-    using Lens = uint4;
-    static __device__ __forceinline__ int code(Codes c, int u)
-    {
-        return (int)(((u < 4 ? c.x : c.y) >> (8 * (u & 3))) & 0xffu);
-    }
-    static __device__ __forceinline__ uint16_t len(Lens r, int u)
-    {
-        const uint32_t w = u < 2 ? r.x : (u < 4 ? r.y : (u < 6 ? r.z : r.w));
-        return (uint16_t)((u & 1) ? (w >> 16) : (w & 0xffffu));
-    }
-    static __device__ __forceinline__ Codes start()
-    {
-        return make_uint2(0x01010101u * kCodeStart, 0x01010101u * kCodeStart);
-    }
-    static __device__ __forceinline__ Lens zero() { return make_uint4(0u, 0u, 0u, 0u); }
-};
 
 __device__ __forceinline__ void unpack_group(const uint8_t* __restrict__ codes,
                                              const uint16_t* __restrict__ lens, float unit, int64_t e0,
