@@ -121,7 +121,15 @@ enum pct_option {
      * the block kernel and one of the apply, so it pays only when several
      * scans share the GPU (pct_solve_batch).  Performance only; PCT_OPT_TIMING does not
      * time the block steps of such a solve. */
-    PCT_OPT_PERSISTENT_BLOCK = 13
+    PCT_OPT_PERSISTENT_BLOCK = 13,
+    /* pct_solve with at least this many DROP blocks per iteration (and at
+     * least 2 iterations, PCT_OPT_TIMING off) records one iteration's block
+     * and apply launches as a CUDA graph on an internal stream (ordered after
+     * and before the context's stream) and replays it once per iteration;
+     * the graph is kept for the next call while x, lambda, the block size and
+     * the context's buffers and options stay the same.  Performance only:
+     * the same kernels with the same arguments.  0 = never.  Default 64. */
+    PCT_OPT_SOLVE_GRAPH = 14
 };
 
 /* Walks of one proton's polyline by one warp (PCT_OPT_WALK). */
@@ -171,8 +179,9 @@ enum pct_stat {
     PCT_STAT_GRAPH_REPLAYS = 11,  /* batched solves replayed from a CUDA graph */
     PCT_STAT_TIMED_LAUNCHES = 12, /* launches of the DROP block kernel timed (PCT_OPT_TIMING) */
     PCT_STAT_BATCH_LANES = 13,    /* lanes per proton of the last batched solve */
-    PCT_STAT_WALK_FALLBACKS = 14  /* DROP row walks PCT_WALK_ROUNDS passed to the lane walk
+    PCT_STAT_WALK_FALLBACKS = 14, /* DROP row walks PCT_WALK_ROUNDS passed to the lane walk
                                      (synchronizes the stream) */
+    PCT_STAT_SOLVE_GRAPH_REPLAYS = 15  /* pct_solve iterations replayed from a CUDA graph */
 };
 
 /* Create a context on CUDA device `device`: the reconstruction volume of

@@ -36,6 +36,8 @@ PCT_STAT_BATCH_LANES = 13
 PCT_OPT_WALK, PCT_WALK_LANES, PCT_WALK_ROUNDS = 12, 0, 1
 PCT_STAT_WALK_FALLBACKS = 14
 PCT_OPT_PERSISTENT_BLOCK = 13
+PCT_OPT_SOLVE_GRAPH = 14
+PCT_STAT_SOLVE_GRAPH_REPLAYS = 15
 PCT_CHORD_FIXED16, PCT_CHORD_FP16 = 0, 1
 (PCT_STAT_LAUNCHES, PCT_STAT_FUSED_LAUNCHES, PCT_STAT_FUSED_MS, PCT_STAT_DEVICE_BYTES,
  PCT_STAT_N_PROTONS, PCT_STAT_N_HULL_VOXELS, PCT_STAT_ROW_ENTRIES, PCT_STAT_ROW_BYTES) = 1, 2, 3, 4, 5, 6, 7, 8

@@ -116,6 +116,13 @@ struct pct_ctx {
     cudaEvent_t batch_ev[2] = {nullptr, nullptr};
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<int64_t> graph_key;
+    // pct_solve: one iteration of block launches captured in a CUDA graph
+    int64_t solve_graph_min = 64;        // fewest blocks per iteration to capture (PCT_OPT_SOLVE_GRAPH; 0 = never)
+    uint64_t gen = 0;                    // bumped by every change of a kernel argument (allocations, options, loads)
+    cudaGraphExec_t solve_exec = nullptr;
+    std::vector<int64_t> solve_key;
+    int64_t solve_launches = 0;          // launches of one captured iteration
+    int64_t solve_replays = 0;
     std::vector<std::vector<int64_t>> tuned_keys;
     std::vector<int> tuned_cta, tuned_lanes;
     std::vector<cudaEvent_t> ev;   // pairs (start, stop) of timed fused launches
@@ -153,6 +160,7 @@ pct_status cuda_fail(pct_ctx* c, cudaError_t e, const char* where)
 pct_status dalloc(pct_ctx* c, void** p, size_t bytes, const char* what)
 {
     *p = nullptr;
+    ++c->gen;
     if (bytes == 0) bytes = 16;
     if (c->mem_cap > 0 && c->mem_used + (int64_t)bytes > c->mem_cap)
         return fail(c, PCT_ERR_OOM, std::string(what) + ": device memory cap exceeded");
@@ -170,6 +178,7 @@ pct_status dalloc(pct_ctx* c, void** p, size_t bytes, const char* what)
 void dfree(pct_ctx* c, void* p)
 {
     if (!p) return;
+    ++c->gen;
     auto it = c->sizes.find(p);
     if (it != c->sizes.end()) {
         c->mem_used -= (int64_t)it->second;
@@ -540,6 +549,7 @@ void pct_destroy(pct_ctx* c)
     c->sizes.clear();
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
     for (cudaEvent_t e : c->batch_ev)
         if (e) cudaEventDestroy(e);
     if (c->batch_stream) cudaStreamDestroy(c->batch_stream);
@@ -560,7 +570,12 @@ pct_status pct_set_option(pct_ctx* c, int32_t key, int64_t value)
 {
     if (!c) return PCT_ERR_ARG;
     DeviceGuard dg(c->device);
+    ++c->gen;
     switch (key) {
+    case PCT_OPT_SOLVE_GRAPH:
+        if (value < 0) return fail(c, PCT_ERR_ARG, "solve graph threshold must be >= 0");
+        c->solve_graph_min = value;
+        return PCT_OK;
     case PCT_OPT_CTA_THREADS:
         if (value < 32 || value > 256 || value % 32) return fail(c, PCT_ERR_ARG, "CTA threads must be 32..256, multiple of 32");
         c->cta = (int)value;
@@ -635,6 +650,7 @@ pct_status pct_get_option(const pct_ctx* c, int32_t key, int64_t* value)
     case PCT_OPT_MODE: *value = c->mode; return PCT_OK;
     case PCT_OPT_CHORD_CODE: *value = c->chord_code; return PCT_OK;
     case PCT_OPT_GRAPH: *value = c->graph; return PCT_OK;
+    case PCT_OPT_SOLVE_GRAPH: *value = c->solve_graph_min; return PCT_OK;
     case PCT_OPT_AUTOTUNE: *value = c->autotune; return PCT_OK;
     case PCT_OPT_BATCH_LANES: *value = c->lanes_opt; return PCT_OK;
     case PCT_OPT_WALK: *value = c->walk; return PCT_OK;
@@ -653,6 +669,7 @@ pct_status pct_load_histories(pct_ctx* c, int64_t n, const float* const in_xyz[3
     if (!c) return PCT_ERR_ARG;
     if (n < 0) return fail(c, PCT_ERR_ARG, "negative proton count");
     DeviceGuard dg(c->device);
+    ++c->gen;
     drop_rows(c);
     c->rec_valid = false;
     if (n == 0) {
@@ -823,6 +840,17 @@ pct_status pct_adjoint(pct_ctx* c, const float* y, float* g)
     return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "adjoint kernel");
 }
 
+// The context's internal stream (batched solves, graph replays of pct_solve) and
+// the two events that order it after and before the context's stream.
+static pct_status ensure_aux_stream(pct_ctx* c)
+{
+    if (c->batch_stream) return PCT_OK;
+    cudaError_t e = cudaStreamCreateWithFlags(&c->batch_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->batch_ev[0], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->batch_ev[1], cudaEventDisableTiming);
+    return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "internal stream");
+}
+
 pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size, float* x)
 {
     if (!c) return PCT_ERR_ARG;
@@ -853,29 +881,84 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
     if (e != cudaSuccess) return cuda_fail(c, e, "accumulator clear");
     const Launch L = launch_of(c);
     const Geo G = geo_of(c);
+    const float* b = c->d_hist ? c->d_hist + (size_t)H_WEPL * c->stride : nullptr;
+    // the block kernel of block `first` and the block apply, with launch shape Lx
+    auto block_kernel = [&](const Launch& Lx, int64_t first) -> cudaError_t {
+        const int64_t count = block_size < c->n - first ? block_size : c->n - first;
+        if (c->mode == PCT_MODE_CSR)
+            return launch_drop_csr(Lx, c->d_flags, c->d_rowptr, c->d_idx, c->d_len, b, first, count, x, c->d_acc);
+        if (c->mode == PCT_MODE_PACKED)
+            return launch_drop_packed(Lx, c->gc, c->d_flags, c->d_rowptr, c->d_start, c->d_codes, c->d_lens16,
+                                      chord_unit(c), b, first, count, x, c->d_acc);
+        return launch_drop_fused(Lx, G, c->d_rec, c->stride, c->d_vidx, c->d_boff, first / block_size, count, x,
+                                 c->d_acc, c->d_next);
+    };
+    auto apply = [&](const Launch& Lx) -> cudaError_t {
+        return launch_drop_apply(Lx, c->n_vox, c->d_mask, x, c->d_acc, lambda, c->d_next);
+    };
+    const int64_t nblocks = (c->n + block_size - 1) / block_size;
+    if (c->solve_graph_min > 0 && nblocks >= c->solve_graph_min && iters >= 2 && c->timing == 0) {
+        if ((s = ensure_aux_stream(c)) != PCT_OK) return s;
+        cudaStream_t bs = c->batch_stream;
+        int32_t lam_bits;
+        std::memcpy(&lam_bits, &lambda, sizeof lam_bits);
+        const std::vector<int64_t> key = {(int64_t)c->gen, (int64_t)(uintptr_t)x, block_size, lam_bits, c->n};
+        if (!c->solve_exec || c->solve_key != key) {
+            if (c->solve_exec) cudaGraphExecDestroy(c->solve_exec);
+            c->solve_exec = nullptr;
+            const int64_t before = c->launches;
+            const Launch Lg{bs, c->cta, &c->launches};
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(c, e, "solve graph capture");
+            for (int64_t first = 0; first < c->n && e == cudaSuccess; first += block_size) {
+                e = block_kernel(Lg, first);
+                if (e == cudaSuccess) e = apply(Lg);
+            }
+            cudaError_t e2 = cudaStreamEndCapture(bs, &g);
+            if (e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                c->launches = before;
+                return cuda_fail(c, e, "DROP kernels (graph capture)");
+            }
+            if (e2 != cudaSuccess) return cuda_fail(c, e2, "solve graph capture");
+            e = cudaGraphInstantiate(&c->solve_exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                c->solve_exec = nullptr;
+                return cuda_fail(c, e, "solve graph instantiate");
+            }
+            c->solve_launches = c->launches - before;
+            c->launches = before;
+            c->solve_key = key;
+        }
+        e = cudaEventRecord(c->batch_ev[0], c->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(bs, c->batch_ev[0], 0);
+        for (int32_t it = 0; it < iters && e == cudaSuccess; ++it) {
+            e = cudaGraphLaunch(c->solve_exec, bs);
+            if (e == cudaSuccess) {
+                ++c->solve_replays;
+                c->launches += c->solve_launches;
+                c->fused_launches += nblocks;
+            }
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(c->batch_ev[1], bs);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, c->batch_ev[1], 0);
+        return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "solve graph launch");
+    }
     for (int32_t it = 0; it < iters; ++it) {
         for (int64_t first = 0; first < c->n; first += block_size) {
-            const int64_t count = block_size < c->n - first ? block_size : c->n - first;
             cudaEvent_t e0 = nullptr, e1 = nullptr;
             if (c->timing > 0 && c->fused_launches % c->timing == 0) {
                 e0 = next_event(c);
                 e1 = next_event(c);
                 if (e0) cudaEventRecord(e0, c->stream);
             }
-            const float* b = c->d_hist ? c->d_hist + (size_t)H_WEPL * c->stride : nullptr;
-            if (c->mode == PCT_MODE_CSR)
-                e = launch_drop_csr(L, c->d_flags, c->d_rowptr, c->d_idx, c->d_len, b, first, count, x, c->d_acc);
-            else if (c->mode == PCT_MODE_PACKED)
-                e = launch_drop_packed(L, c->gc, c->d_flags, c->d_rowptr, c->d_start, c->d_codes, c->d_lens16,
-                                       chord_unit(c), b,
-                                       first, count, x, c->d_acc);
-            else
-                e = launch_drop_fused(L, G, c->d_rec, c->stride, c->d_vidx, c->d_boff, first / block_size,
-                                      count, x, c->d_acc, c->d_next);
+            e = block_kernel(L, first);
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP kernel");
             ++c->fused_launches;
             if (e1) cudaEventRecord(e1, c->stream);
-            e = launch_drop_apply(L, c->n_vox, c->d_mask, x, c->d_acc, lambda, c->d_next);
+            e = apply(L);
             if (e != cudaSuccess) return cuda_fail(c, e, "DROP apply kernel");
         }
     }
@@ -1257,12 +1340,7 @@ pct_status pct_solve_batch(pct_ctx* const* ctxs, int32_t count, const int32_t* i
         c0->d_bnext = (unsigned long long*)p;
         c0->scan_cap = count;
     }
-    if (!c0->batch_stream) {
-        cudaError_t e = cudaStreamCreateWithFlags(&c0->batch_stream, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c0->batch_ev[0], cudaEventDisableTiming);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c0->batch_ev[1], cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(c0, e, "batch stream");
-    }
+    if (pct_status sa = ensure_aux_stream(c0); sa != PCT_OK) return sa;
     // CTA size and lanes per proton: autotuned (fastest of 128 / 256 threads x
     // 32 / 16 lanes per proton on one iteration, on scratch copies of x), or
     // the context's options
@@ -1482,6 +1560,7 @@ pct_status pct_get_stat(pct_ctx* c, int32_t key, double* value)
     case PCT_STAT_BATCH_CTAS: *value = (double)c->batch_ctas; return PCT_OK;
     case PCT_STAT_BATCH_LANES: *value = (double)c->batch_lanes; return PCT_OK;
     case PCT_STAT_GRAPH_REPLAYS: *value = (double)c->graph_replays; return PCT_OK;
+    case PCT_STAT_SOLVE_GRAPH_REPLAYS: *value = (double)c->solve_replays; return PCT_OK;
     case PCT_STAT_WALK_FALLBACKS: {
         unsigned long long v = 0;
         cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -111,12 +111,12 @@ def test_adjoint_matches_oracle_and_identity(tiny):
     assert abs(lhs - rhs) <= 1e-5 * (np.abs(ax) @ np.abs(yv) + 1.0)
 
 
-@pytest.mark.parametrize("persistent", [0, 3200])
+@pytest.mark.parametrize("launch", ["direct", "persistent", "graph"])
 @pytest.mark.parametrize("lam", [1e-4, 0.5])
-def test_drop_solve_matches_oracle(tiny, lam, persistent):
+def test_drop_solve_matches_oracle(tiny, lam, launch):
     """Final RSP after 6 iterations at block size 3200 (ragged last block), with
-    a launch per block step and (persistent = 3200) with all block steps in one
-    persistent launch.
+    a launch per block step, with all block steps in one persistent launch, and
+    with each iteration's launches replayed from a CUDA graph.
 
     Every hull voxel that the comparison rule keeps (its DROP count s_j is the
     same on both sides in every block, and no oracle-flagged near-face row
@@ -127,16 +127,21 @@ def test_drop_solve_matches_oracle(tiny, lam, persistent):
     cfg, ctx, hull = tiny["cfg"], tiny["ctx"], tiny["hull"]
     x0 = hull.astype(np.float32)
     x = torch.from_numpy(x0).cuda()
-    ctx.set_option(pct.PCT_OPT_PERSISTENT_BLOCK, persistent)
+    persistent = launch == "persistent"
+    ctx.set_option(pct.PCT_OPT_PERSISTENT_BLOCK, cfg.block if persistent else 0)
+    ctx.set_option(pct.PCT_OPT_SOLVE_GRAPH, 1 if launch == "graph" else 0)
     try:
         launches = ctx.stat(pct.PCT_STAT_LAUNCHES)
+        replays = ctx.stat(pct.PCT_STAT_SOLVE_GRAPH_REPLAYS)
         ctx.solve(x, cfg.iters, lam, cfg.block)
         ctx.synchronize()
         if persistent:
             # one launch for the whole solve (plus the block lists built once)
             assert ctx.stat(pct.PCT_STAT_LAUNCHES) - launches <= 4
+        assert ctx.stat(pct.PCT_STAT_SOLVE_GRAPH_REPLAYS) - replays == (cfg.iters if launch == "graph" else 0)
     finally:
         ctx.set_option(pct.PCT_OPT_PERSISTENT_BLOCK, 0)
+        ctx.set_option(pct.PCT_OPT_SOLVE_GRAPH, 64)
     xg = x.cpu().numpy().astype(np.float64)
     xo = O.drop(tiny["A"], tiny["hist"]["wepl"].astype(np.float64), cfg.iters, lam, cfg.block,
                 x0.astype(np.float64))
@@ -165,3 +170,35 @@ def test_solve_host_equals_device_solve(tiny):
     hm = hull.astype(bool)
     # same kernels, same inputs: only the order of FP32 atomics differs
     assert np.max(np.abs(xh - xd)[hm] / xd[hm]) <= 1e-4
+
+
+def test_solve_graph_is_reused_and_rebuilt(tiny):
+    """The captured iteration is replayed by a second call with the same
+    arguments and captured again for a new x; every form gives the same
+    iterate as direct launches (up to the order of FP32 atomics)."""
+    cfg, ctx, hull = tiny["cfg"], tiny["ctx"], tiny["hull"]
+    x0 = hull.astype(np.float32)
+    hm = hull.astype(bool)
+    xd = torch.from_numpy(x0).cuda()
+    ctx.set_option(pct.PCT_OPT_SOLVE_GRAPH, 0)
+    ctx.solve(xd, 2, 0.5, cfg.block)
+    ref = xd.cpu().numpy()
+    ctx.set_option(pct.PCT_OPT_SOLVE_GRAPH, 1)
+    try:
+        out = []
+        xg = torch.from_numpy(x0).cuda()
+        for _ in range(2):   # the same x: the second call replays the kept graph
+            xg.copy_(torch.from_numpy(x0).cuda())
+            r0 = ctx.stat(pct.PCT_STAT_SOLVE_GRAPH_REPLAYS)
+            ctx.solve(xg, 2, 0.5, cfg.block)
+            ctx.synchronize()
+            assert ctx.stat(pct.PCT_STAT_SOLVE_GRAPH_REPLAYS) - r0 == 2
+            out.append(xg.cpu().numpy())
+        x2 = torch.from_numpy(x0).cuda()   # a new x pointer: captured again
+        ctx.solve(x2, 2, 0.5, cfg.block)
+        out.append(x2.cpu().numpy())
+    finally:
+        ctx.set_option(pct.PCT_OPT_SOLVE_GRAPH, 64)
+    for xg in out:
+        assert np.max(np.abs(xg - ref)[hm] / ref[hm]) <= 1e-4
+        assert np.array_equal(xg[~hm], x0[~hm])
