@@ -118,8 +118,9 @@ enum pct_option {
      * its device errors and barrier timeouts are reported by pct_synchronize).
      * 0 = never.  Default 0: on the head workload (1e7 protons, block 3200)
      * a block step measured 27.2 us this way against 24.8 us with a launch of
-     * the block kernel and one of the apply, so it pays only when several
-     * scans share the GPU (pct_solve_batch).  Performance only; PCT_OPT_TIMING does not
+     * the block kernel and one of the apply (18.2 us with those launches
+     * replayed from a graph, PCT_OPT_SOLVE_GRAPH), so it pays only when
+     * several scans share the GPU (pct_solve_batch).  Performance only; PCT_OPT_TIMING does not
      * time the block steps of such a solve. */
     PCT_OPT_PERSISTENT_BLOCK = 13,
     /* pct_solve with at least this many DROP blocks per iteration (and at
