@@ -39,7 +39,7 @@ struct Geo {
 // 1/(beta^2 p^2) of a 200 MeV proton in water as a polynomial in depth (cm),
 // MeV^-2: the energy-loss fit used with the most-likely-path formalism (host).
 extern const double kCoef200[6];
-// MLP table tab[k] = Sigma(0, k du) (S00, S01, S11, 0) in cm / rad for
+// MLP table tab[k] = Sigma(0, k du) (S00, S01, S11, 2 S01) in cm / rad for
 // k = 0..kmax (tab[0] = 0), evaluated in FP64 on the host.
 void mlp_sigma_table(double du_mm, int kmax, float4* tab);
 

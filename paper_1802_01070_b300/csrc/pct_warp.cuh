@@ -11,10 +11,13 @@
 // shuffle repairs the squared norm (+2ab) and decides which lane owns such a run
 // for the DROP count and scatter.
 //
-// Pass 1 (walk): every lane stores its hull runs (voxel, chord) in shared
-// memory, accumulates s = a_i.x and q = ||a_i||^2 and records its first and last
-// raw run.  Later passes replay the stored runs instead of recomputing the MLP
-// and the walk; a lane with more runs than its slots re-walks its range.
+// Pass 1 (walk): every lane stores its hull runs as (voxel, chord) pairs in
+// shared memory and accumulates s = a_i.x and q = ||a_i||^2; the hull byte and
+// x of a voxel are loaded when the walk steps into it and used when the run
+// there ends (EntrySink), and the lane's first and last raw runs are the runs
+// in the voxels its range starts and ends in.  Later passes replay the stored
+// runs instead of recomputing the MLP and the walk; a lane with more runs than
+// its slots re-walks its range.
 #pragma once
 
 #include "pct_device.cuh"
