@@ -442,6 +442,8 @@ def run_ours(args):
                               "this kernel source",
                 "hbm_gbs_algorithmic": hbm_bytes_launch / avg_launch_s / 1e9,
                 "hbm_peak_gbs": peaks.get("hbm_gbs"),
+                "hbm_frac_algorithmic": (hbm_bytes_launch / avg_launch_s / 1e9 / peaks["hbm_gbs"]
+                                         if peaks.get("hbm_gbs") else None),
                 "fused_share_of_step": avg_launch_s * 1e3 * fused_n / args.steps / step_ms
                 if step_ms else None}
     if args.mode != "fused":
