@@ -124,9 +124,10 @@ enum pct_option {
      * time the block steps of such a solve. */
     PCT_OPT_PERSISTENT_BLOCK = 13,
     /* pct_solve with at least this many DROP blocks per iteration (and at
-     * least 2 iterations, PCT_OPT_TIMING off) records one iteration's block
-     * and apply launches as a CUDA graph on an internal stream (ordered after
-     * and before the context's stream) and replays it once per iteration;
+     * most 8192, at least 2 iterations, PCT_OPT_TIMING off) records one
+     * iteration's block and apply launches as a CUDA graph on an internal
+     * stream (ordered after and before the context's stream) and replays it
+     * once per iteration;
      * the graph is kept for the next call while x, lambda, the block size and
      * the context's buffers and options stay the same.  Performance only:
      * the same kernels with the same arguments.  0 = never.  Default 64. */

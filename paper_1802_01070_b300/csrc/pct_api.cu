@@ -840,6 +840,8 @@ pct_status pct_adjoint(pct_ctx* c, const float* y, float* g)
     return e == cudaSuccess ? PCT_OK : cuda_fail(c, e, "adjoint kernel");
 }
 
+constexpr int64_t kSolveGraphMaxBlocks = 8192;
+
 // The context's internal stream (batched solves, graph replays of pct_solve) and
 // the two events that order it after and before the context's stream.
 static pct_status ensure_aux_stream(pct_ctx* c)
@@ -897,7 +899,10 @@ pct_status pct_solve(pct_ctx* c, int32_t iters, float lambda, int64_t block_size
         return launch_drop_apply(Lx, c->n_vox, c->d_mask, x, c->d_acc, lambda, c->d_next);
     };
     const int64_t nblocks = (c->n + block_size - 1) / block_size;
-    if (c->solve_graph_min > 0 && nblocks >= c->solve_graph_min && iters >= 2 && c->timing == 0) {
+    // capture and instantiation cost ~2.3 us per node: beyond kSolveGraphMaxBlocks blocks per
+    // iteration (torso at B = 3200: 36250) it outweighs the launch gaps the replay saves
+    if (c->solve_graph_min > 0 && nblocks >= c->solve_graph_min && nblocks <= kSolveGraphMaxBlocks &&
+        iters >= 2 && c->timing == 0) {
         if ((s = ensure_aux_stream(c)) != PCT_OK) return s;
         cudaStream_t bs = c->batch_stream;
         int32_t lam_bits;
