@@ -17,7 +17,7 @@ between blocks, as the Gauss-Seidel sequence of blocks requires).  Reported:
   isolates the rows (FP32 paths resolving near-face crossings differently).
 
 Usage (GPU machine; one full iteration takes the oracle ~30-40 min on 16 cores):
-    python tests/torso_full_parity.py --iters 1 --every 24 --out gpurun_out/torso_parity.json
+    python tests/torso_full_parity.py --iters 1 --every 24 --out torso_parity.json
 Writes the JSON summary after every sampled block, so a cut-short run keeps
 what it measured.
 """
