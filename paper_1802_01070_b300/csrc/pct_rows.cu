@@ -448,12 +448,7 @@ k_drop_csr(unsigned* flags, const int64_t* __restrict__ rowptr, const int32_t* _
         atomicAdd(acc + __ldg(idx + e), make_float2(__ldg(len + e) * r, 1.f));
 }
 
-// Decode the 32 * kPackAlign entries of a packed row starting at e0 (a whole
-// group): lane l takes entries e0 + kPackAlign * l .. + kPackAlign - 1 with one
-// load of their codes and one of their chords, sums their steps in the lane,
-// and one warp scan of the lanes' sums places them.  (bx, by, bz) is the voxel
-// before e0 and is advanced past the group.  Entries at or beyond e1 decode as
-// outside the hull.
+// The codes and chords of a lane's kPackAlign entries as one load each.
 template <int V>
 struct PackVec;
 template <>
@@ -470,6 +465,12 @@ struct PackVec<4> {
     static __device__ __forceinline__ Lens zero() { return make_uint2(0u, 0u); }
 };
 
+// Decode the 32 * kPackAlign entries of a packed row starting at e0 (a whole
+// group): lane l takes entries e0 + kPackAlign * l .. + kPackAlign - 1 with one
+// load of their codes and one of their chords, sums their steps in the lane,
+// and one warp scan of the lanes' sums places them.  (bx, by, bz) is the voxel
+// before e0 and is advanced past the group.  Entries at or beyond e1 decode as
+// outside the hull.
 __device__ __forceinline__ void unpack_group(const uint8_t* __restrict__ codes,
                                              const uint16_t* __restrict__ lens, float unit, int64_t e0,
                                              int64_t e1, int& bx, int& by, int& bz, const Dims& g,
