@@ -303,7 +303,9 @@ pct_status pct_adjoint(pct_ctx *ctx, const float *y, float *g);
  * where s_j counts the rows of the block that cross voxel j (voxels no row
  * crosses are unchanged; empty rows are skipped).
  *   x -- device, n float32: the initial iterate on entry, the RSP on return.
- * Enqueued on the context stream; pct_synchronize reports device errors.
+ * Enqueued on the context stream (a solve of many small blocks may run its
+ * launches from a CUDA graph on the context's internal stream, ordered after
+ * and before it: PCT_OPT_SOLVE_GRAPH); pct_synchronize reports device errors.
  * Errors: PCT_ERR_ARG (null x, iters < 0, block_size < 1), PCT_ERR_STATE,
  * PCT_ERR_OOM, PCT_ERR_CUDA. */
 pct_status pct_solve(pct_ctx *ctx, int32_t iters, float lambda, int64_t block_size, float *x);
